@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Throughput of the Vegas hot path on one B300 (or N independent replicas).
+
+Workload (one "step"): the d=8 Lepage Gaussian (Eq. 1, a = 0.1, centres 1/2),
+50 bins per dimension, uniform starting grid, damping alpha = 1.5:
+10 adapting iterations of 1e7 samples (each followed by a grid refinement),
+then 5 fixed-grid iterations of 1e8 samples -- 6e8 samples per step.  The
+headline value is samples/s of the FP32-eval / FP64-accumulate path; the plain
+FP64 path runs the same workload (same counters, hence equal error) and is
+reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own replica (own seeds, no collective on the
+data path); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Vegas samples/s, d=8 Gaussian: FP32-eval vs plain FP64 at equal error; % FP peak"
+DIM, NBINS, A, ALPHA = 8, 50, 0.1, 1.5
+N_ADAPT, IT_ADAPT, N_FIXED, IT_FIXED = 10_000_000, 10, 100_000_000, 5
+SAMPLES_PER_STEP = N_ADAPT * IT_ADAPT + N_FIXED * IT_FIXED
+WORKLOAD = "gauss_d8_a0.1_N50_10x1e7adapt+5x1e8fixed"
+EXACT = math.erf(0.5 / A) ** DIM
+
+# Issue-slot peak from unit counts and clock: 148 SMs x 4 schedulers x 32 lanes
+# at the 2032 MHz maximum SM clock (lane-instructions per second).
+SMS, LANES_PER_SM, SM_MAX_MHZ = 148, 128, 2032.0
+ALU_PEAK_TOPS = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+
+# DRAM bytes per launch of the fixed-grid FP32 iterate kernel from the ncu
+# capture summarised in profiles/ (None until captured for this kernel build).
+ITERATE_TRAFFIC_BYTES = None
+
+
+def alg_ops_per_sample(d):
+    """Algorithmic lane-operations of one FP32 fixed-grid sample: Philox (10
+    rounds x 2 wide multiplies + 2 three-input xors per call), per dimension
+    bin/position multiplies, fraction (2), grid load, map fma, Jacobian multiply
+    and two integrand fmas (9), one N^4 multiply per call, and 13 per sample
+    (exponential 2, weight 1, Kahan 8 + square 1, finiteness 1)."""
+    calls = (d + 3) // 4
+    return 40 * calls + 9 * d + calls + 13
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while it runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(device_index)], stdout=self.file,
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) == 8:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[0]) for r in rows if num(r[0])]
+        mx = [num(r[1]) for r in rows if num(r[1])]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        loaded = [s for s in sm if s >= 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows),
+                "power_w_max": max((num(r[2]) or 0.0) for r in rows)}
+
+
+def l2_flush(buf):
+    buf.zero_()
+
+
+def run_step(V, ws, stream, mode, seed, fixed_events=None):
+    """Enqueue one whole workload step; returns the handle (not synchronised)."""
+    import torch
+
+    from paper_2002_12921_b300 import workloads as W
+
+    h = V.vegas_init_grid(DIM, NBINS, seed, mode, V.VEGAS_GAUSS, W.gauss_params(DIM, A),
+                          IT_ADAPT + IT_FIXED, ws.data_ptr(), ws.numel(), stream.cuda_stream)
+    for _ in range(IT_ADAPT):
+        V.vegas_iterate(h, N_ADAPT, 1)
+        V.vegas_refine(h, ALPHA)
+    for _ in range(IT_FIXED):
+        if fixed_events is not None:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            V.vegas_iterate(h, N_FIXED, 0)
+            e1.record(stream)
+            fixed_events.append((e0, e1))
+        else:
+            V.vegas_iterate(h, N_FIXED, 0)
+    return h
+
+
+LAUNCHES_PER_STEP = 1 + IT_ADAPT * 2 + IT_FIXED  # init, iterate+refine, fixed iterate
+
+
+def time_mode(V, mode, steps, warmup, seed0, ws, flush, stream):
+    """Device time of `steps` whole steps (events on the library's stream)."""
+    import torch
+
+    handles = []
+    for w in range(warmup):
+        handles.append(run_step(V, ws, stream, mode, seed0 + 1000 + w))
+    torch.cuda.synchronize()
+    step_events, fixed = [], []
+    for s in range(steps):
+        l2_flush(flush)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        handles.append(run_step(V, ws, stream, mode, seed0 + s, fixed))
+        e1.record(stream)
+        step_events.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in step_events]
+    fixed_ms = [a.elapsed_time(b) for a, b in fixed]
+    last = handles[-1]
+    res = V.vegas_result(last, IT_ADAPT)
+    for h in handles:
+        V.vegas_destroy(h)
+    return ms, fixed_ms, res
+
+
+def e2e_mode(V, mode, steps, seed0, ws, stream):
+    """Same workload through the public API with host buffers: per step the
+    starting grid and the integrand parameters come from pinned host memory and
+    the iteration log is read back to the host for the combined result."""
+    import numpy as np
+    import torch
+
+    from paper_2002_12921_b300 import workloads as W
+
+    grid = torch.empty((DIM, NBINS + 1), dtype=torch.float64).pin_memory()
+    grid.copy_(torch.from_numpy(np.tile(np.arange(NBINS + 1) / NBINS, (DIM, 1))))
+    grid_np = grid.numpy()
+    params = W.gauss_params(DIM, A)
+    times = []
+    for s in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = V.vegas_init_grid(DIM, NBINS, seed0 + s, mode, V.VEGAS_GAUSS, params,
+                              IT_ADAPT + IT_FIXED, ws.data_ptr(), ws.numel(), stream.cuda_stream)
+        V.vegas_set_grid(h, grid_np)
+        for _ in range(IT_ADAPT):
+            V.vegas_iterate(h, N_ADAPT, 1)
+            V.vegas_refine(h, ALPHA)
+        for _ in range(IT_FIXED):
+            V.vegas_iterate(h, N_FIXED, 0)
+        V.vegas_result(h, IT_ADAPT)
+        times.append(time.perf_counter() - t0)
+        V.vegas_destroy(h)
+    h2d = DIM * (NBINS + 1) * 8 + len(params) * 8
+    d2h = (IT_ADAPT + IT_FIXED) * 8 * 8 + 64 * 4
+    return times, h2d, d2h
+
+
+def cpu_baseline(fast=False):
+    """The FP64 CPU oracle, as it stands, on all host cores, on a bounded sample
+    of the workload: 2 adapting iterations of 1e7 then 2 fixed-grid iterations
+    of 2e7 samples (6e7 samples)."""
+    import oracle
+    from paper_2002_12921_b300 import workloads as W
+
+    cores = os.cpu_count() or 1
+    sched = [(N_ADAPT, 1)] * 2 + [(2 * N_ADAPT, 0)] * 2
+    if fast:
+        sched = [(N_ADAPT // 2, 1), (N_ADAPT, 0)]
+    oracle.lib()
+    t0 = time.perf_counter()
+    r = oracle.run(DIM, NBINS, 2, W.GAUSS, W.gauss_params(DIM, A), sched, alpha=ALPHA,
+                   nthreads=cores)
+    dt = time.perf_counter() - t0
+    n = sum(s for s, _ in sched)
+    return {"value": n / dt, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": f"{WORKLOAD}: " + " + ".join(f"{s:.0e}{'a' if a else 'f'}" for s, a in sched)
+            + f" = {n:.1e} samples, FP64, {cores} threads", "seconds": dt,
+            "result": r["mean"]}
+
+
+def reference_arm(args, rank, world):
+    """The oracle timed as the reference implementation (rank 0 only)."""
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_baseline(fast=True)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        cb = cpu_baseline(fast=True)
+        vals.append(cb["value"])
+        secs.append(cb["seconds"])
+    value = statistics.median(vals)
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.median(secs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "dim": DIM, "nbins": NBINS,
+                       "sample_per_step": cb["sample"]},
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cb["cores"],
+                             "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    import torch
+
+    import paper_2002_12921_b300 as V
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    V.lib()
+    stream = torch.cuda.current_stream()
+    ws = torch.empty(V.vegas_workspace_bytes(DIM, NBINS, IT_ADAPT + IT_FIXED), dtype=torch.uint8,
+                     device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    seed0 = 2 + 100_000 * rank
+
+    # FP32-eval (headline), with clocks sampled during the timed steps
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device())
+    ms32, fixed32, res32 = time_mode(V, V.VEGAS_FP32_EVAL, args.steps, max(3, args.warmup),
+                                     seed0, ws, flush, stream)
+    clk = clocks.stop()
+    total_ms = sum(ms32)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = SAMPLES_PER_STEP * args.steps * world / (total_ms / 1e3)
+
+    # plain FP64 on the same counters (equal error)
+    ms64, fixed64, res64 = time_mode(V, V.VEGAS_FP64, args.fp64_steps, 1, seed0, ws, flush,
+                                     stream)
+    value64 = SAMPLES_PER_STEP * args.fp64_steps / (sum(ms64) / 1e3)
+
+    # end to end through the public API with host buffers
+    e2e_t, h2d, d2h = e2e_mode(V, V.VEGAS_FP32_EVAL, max(3, min(args.steps, 5)), seed0, ws,
+                               stream)
+    e2e_value = SAMPLES_PER_STEP / statistics.median(e2e_t)
+
+    fixed_ms = statistics.mean(fixed32)
+    ops = alg_ops_per_sample(DIM) * N_FIXED
+    achieved = ops / (fixed_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS,
+                "unit": "Tops/s", "frac": achieved / ALU_PEAK_TOPS,
+                "traffic": ITERATE_TRAFFIC_BYTES,
+                "kernel": "vegas_iterate_kernel<float,8,GAUSS,fixed>",
+                "kernel_ms": fixed_ms, "ops_per_sample": alg_ops_per_sample(DIM),
+                "peak_basis": "148 SMs x 128 lanes x 2032 MHz (recipe unit counts and max clock)"}
+    if clk.get("sm_mhz"):
+        roofline["frac_at_measured_clock"] = achieved / (SMS * LANES_PER_SM * clk["sm_mhz"] * 1e6
+                                                         / 1e12)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline()
+        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    if rank == 0:
+        m32, s32 = res32[0], res32[1]
+        m64, s64 = res64[0], res64[1]
+        line = {
+            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dim": DIM, "nbins": NBINS, "a": A, "alpha": ALPHA,
+                       "samples_per_step": SAMPLES_PER_STEP, "mode": "fp32_eval_fp64_accumulate",
+                       "l2": "256 MiB buffer written between timed steps, outside the step events",
+                       "parallelism": f"{world} independent replicas"},
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "fp64_plain": {"value": value64, "unit": "samples/s",
+                           "ms_per_step": sum(ms64) / args.fp64_steps,
+                           "kernel_ms_fixed_iteration": statistics.mean(fixed64)},
+            "speedup_fp32_over_fp64": value / value64,
+            "result": {"fp32": {"mean": m32, "sigma": s32, "pull": (m32 - EXACT) / s32},
+                       "fp64": {"mean": m64, "sigma": s64, "pull": (m64 - EXACT) / s64},
+                       "exact": EXACT, "sigma_ratio_fp32_fp64": s32 / s64,
+                       "abs_diff_fp32_fp64_in_sigma": abs(m32 - m64) / s64},
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

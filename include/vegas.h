@@ -1,0 +1,183 @@
+/*
+ * vegas.h -- C ABI of the B300 (sm_103a) Vegas hot path.
+ *
+ * One Vegas iteration (VegasFlow, Sec. 2.2: the per-event step, then the
+ * after-iteration refinement; the method is Lepage's, cited in Sec. 1):
+ *   vegas_iterate  draws n samples from counter-based Philox4x32-10, maps them
+ *                  through the adaptive grid, evaluates the integrand and
+ *                  reduces sum fJ, sum (fJ)^2 and the per-dimension per-bin
+ *                  (fJ)^2 histogram -- one fused kernel;
+ *   vegas_refine   smooths, damps and re-partitions the grid from the
+ *                  histogram -- one small kernel, device only;
+ *   vegas_result   combines the iterations (inverse-variance weights) on the
+ *                  host.
+ *
+ * Memory and streams.  The caller owns all device memory: it passes one
+ * workspace buffer of vegas_workspace_bytes() bytes (any allocator; 256-byte
+ * aligned) and a CUDA stream (cudaStream_t as void*, NULL = legacy default
+ * stream).  The library never allocates device memory.  It owns only the small
+ * host-side descriptor returned by vegas_init_grid.  Every call that launches
+ * work is asynchronous on the stream; vegas_result, vegas_get_* synchronise it.
+ *
+ * Errors.  Every function returns a status (VEGAS_OK = 0).  No C++ exception
+ * and no abort crosses the ABI.  Asynchronous device errors surface at the next
+ * synchronising call.  A state whose call failed with VEGAS_ECUDA should be
+ * destroyed.
+ *
+ * Sample counters.  Sample i (0-based, 64-bit, counted across launches of one
+ * iteration) of iteration t draws Philox4x32-10 under key (seed low word, seed
+ * high word) at counter (i low, i high, q | integral_id << 8, t) for
+ * q = 0 .. ceil(dim/4)-1; dimension k takes word k mod 4 of call q = k/4.  The
+ * result is therefore a pure function of (seed, grid, n, t), independent of
+ * launch configuration and chunking.
+ *
+ * Bin and position.  For word w: bin j = floor(w N / 2^32) (exact integer),
+ * position l = (w N) mod 2^32.  FP64 mode: frac = (l + 1/2) 2^-32.  FP32 mode:
+ * frac = (floor(l / 2^9) + 1/2) 2^-23.  x = e_j + frac (e_{j+1} - e_j),
+ * J = prod_k N (e_{j+1} - e_j).  In FP32 mode e_j, e_{j+1} are first rounded to
+ * float and their difference is taken in float, so the map stays an exact
+ * change of variables of the rounded grid.
+ */
+#ifndef VEGAS_B300_VEGAS_H
+#define VEGAS_B300_VEGAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define VEGAS_OK 0
+#define VEGAS_EINVAL 1     /* an argument is out of range or NULL */
+#define VEGAS_ECUDA 2      /* a CUDA runtime call failed (launch or sync) */
+#define VEGAS_ENONFINITE 3 /* some f*J was NaN or infinite (left out of the sums) */
+#define VEGAS_ESTATE 4     /* call out of order, iteration log full, bad grid */
+#define VEGAS_ENOSPACE 5   /* workspace smaller than vegas_workspace_bytes() */
+
+/* ---- precision modes ---------------------------------------------------- */
+#define VEGAS_FP64 0      /* map, integrand and sums in double */
+#define VEGAS_FP32_EVAL 1 /* map and integrand in float; per-thread compensated
+                             (Kahan) float sums, double above the thread; grid,
+                             histogram, refinement and combination in double */
+
+/* ---- built-in integrands over [0,1]^dim (VegasFlow Sec. 3.1) ------------- */
+/* VEGAS_GAUSS      Eq. 1, per-dimension centres:
+ *                  f = (a sqrt(pi))^-d exp(-sum_k (x_k - mu_k)^2 / a^2);
+ *                  params = [a, mu_1 .. mu_d]            (nparams = 1 + d)
+ *                  integral = prod_k (erf((1-mu_k)/a) + erf(mu_k/a)) / 2.
+ * VEGAS_GAUSS_MIX2 (G(x; muA, a) + G(x; muB, a)) / 2 with G the Eq. 1 term;
+ *                  params = [a, muA_1 .. muA_d, muB_1 .. muB_d] (1 + 2d).
+ * VEGAS_FLAT       f = 1; params ignored (nparams may be 0).
+ * VEGAS_GENZ_DISC  Eq. 2 normalised to integrate to 1: 0 if any x_k <= a_k,
+ *                  else exp(sum_k c_k x_k) / prod_k (e^{c_k} - e^{c_k a_k})/c_k;
+ *                  params = [a_1 .. a_d, c_1 .. c_d] (2d), c_k != 0.
+ * VEGAS_GENZ_PPEAK Eq. 3 normalised to integrate to 1:
+ *                  prod_k 1/(c_k^-2 + (x_k - a_k)^2) / (c_k (atan(c_k (1-a_k)) +
+ *                  atan(c_k a_k))); params = [a_1 .. a_d, c_1 .. c_d] (2d), c_k > 0. */
+#define VEGAS_GAUSS 0
+#define VEGAS_GAUSS_MIX2 1
+#define VEGAS_FLAT 2
+#define VEGAS_GENZ_DISC 3
+#define VEGAS_GENZ_PPEAK 4
+
+/* ---- limits --------------------------------------------------------------- */
+#define VEGAS_MAX_DIM 16
+#define VEGAS_MAX_BINS 1024
+#define VEGAS_MAX_DIM_X_BINS 8192 /* dim * nbins (shared-memory grid copy) */
+
+typedef struct vegas_state vegas_state; /* opaque host descriptor */
+
+/* Launch configuration; zeros select the defaults. */
+typedef struct {
+    int block_threads;    /* threads per block of the iterate kernel (multiple of 32,
+                             32 .. 256); default 256 */
+    int blocks_per_sm;    /* resident blocks per SM the grid is sized for; default:
+                             the occupancy limit */
+    int min_samples_per_thread; /* the grid shrinks so that every thread gets at least
+                                   this many samples; default 8 */
+    uint64_t chunk_samples;     /* samples per launch inside one iteration; 0 = one
+                                   launch per iteration */
+} vegas_config;
+
+/* Bytes of device workspace for a state of this shape with room for max_iters
+ * iterations in its device log.  dim in [1, 16], nbins in [1, 1024],
+ * dim*nbins <= 8192, max_iters >= 1.  Returns VEGAS_EINVAL otherwise. */
+int vegas_workspace_bytes(int dim, int nbins, int max_iters, size_t *bytes);
+
+/* Create a state: uniform grid e_l = l/nbins in every dimension (Lepage 1978,
+ * Sec. 2: the starting grid), zero histogram, empty iteration log.
+ *   mode       VEGAS_FP64 or VEGAS_FP32_EVAL
+ *   integrand  one of the VEGAS_* integrand ids, params as documented above
+ *              (copied; the caller may free them on return)
+ *   d_workspace, ws_bytes  device buffer owned by the caller; it must outlive
+ *              the state and must not be used by anything else meanwhile
+ *   cuda_stream  the stream all work of this state is ordered on
+ * On success *out receives the descriptor.  Asynchronous: the workspace is
+ * initialised by work enqueued on the stream. */
+int vegas_init_grid(vegas_state **out, int dim, int nbins, uint64_t seed, int mode, int integrand,
+                    const double *params, int nparams, int max_iters, void *d_workspace,
+                    size_t ws_bytes, void *cuda_stream);
+
+/* Change the launch configuration (cfg == NULL restores the defaults). */
+int vegas_set_config(vegas_state *s, const vegas_config *cfg);
+
+/* Run one iteration of n_samples >= 2 samples on the current grid (the
+ * per-event step of Sec. 2.2).  adapt != 0 also adds each sample's (fJ)^2 to
+ * the histogram bin of each dimension for the next vegas_refine.  Appends
+ * (S1, S2, n, nonfinite, I = S1/n, var = (S2/n - I^2)/(n-1)) to the device log.
+ * Asynchronous; VEGAS_ESTATE if the log is full. */
+int vegas_iterate(vegas_state *s, uint64_t n_samples, int adapt);
+
+/* Refine the grid from the accumulated histogram and clear it (the
+ * after-iteration step of Sec. 2.2; Lepage 1978 Sec. 3 and the 1980 report):
+ * per dimension, three-point smoothing (the two end bins averaged with their
+ * one neighbour), normalisation r_j = h_j / sum h, damping
+ * m_j = ((r_j - 1)/ln r_j)^alpha, and new edges where the piecewise-linear
+ * cumulative m reaches l * sum(m)/N, l = 1..N-1.  A dimension whose histogram
+ * sums to 0 or is not finite keeps its grid.  alpha >= 0.  Device only,
+ * asynchronous. */
+int vegas_refine(vegas_state *s, double alpha);
+
+/* Combine iterations first_iter .. n_iter-1 (inverse-variance weighted mean,
+ * sigma = (sum 1/var)^-1/2, chi^2 per degree of freedom; an iteration with
+ * zero variance makes it the plain mean with sigma 0).  Synchronises the
+ * stream.  Any output pointer may be NULL.  Returns VEGAS_ENONFINITE (after
+ * filling the outputs) if a combined iteration saw non-finite f*J. */
+int vegas_result(vegas_state *s, int first_iter, double *mean, double *sigma, double *chi2_dof,
+                 int *n_iter);
+
+/* Copy the log to host memory: row t = {S1, S2, n, nonfinite, I, var} for
+ * t < min(max_rows, n_iter).  Synchronises the stream. */
+int vegas_get_iterations(vegas_state *s, double *host_rows, int max_rows, int *n_rows);
+
+/* Copy the grid (dim x (nbins+1) doubles, row-major) to / from host memory.
+ * vegas_set_grid checks e_0 = 0, e_N = 1 and strict increase (VEGAS_ESTATE
+ * otherwise).  Both synchronise the stream. */
+int vegas_get_grid(vegas_state *s, double *host_edges);
+int vegas_set_grid(vegas_state *s, const double *host_edges);
+
+/* Copy the histogram (dim x nbins doubles) to host memory.  Synchronises. */
+int vegas_get_histogram(vegas_state *s, double *host_hist);
+
+/* Write the Philox4x32-10 words that samples i0 .. i0+n-1 of iteration iter
+ * draw (the counter layout above) to d_out, n x dim uint32 rows in device
+ * memory owned by the caller; the same device function the iterate kernel
+ * uses.  A reproducibility and test aid.  dim in [1, 16]; asynchronous on the
+ * stream. */
+int vegas_sample_words(uint64_t seed, uint32_t integral_id, uint32_t iter, uint64_t i0,
+                       uint64_t n, int dim, uint32_t *d_out, void *cuda_stream);
+
+/* Release the descriptor (not the caller's workspace).  Synchronises the
+ * stream first.  NULL is accepted. */
+int vegas_destroy(vegas_state *s);
+
+/* Static text for a status code. */
+const char *vegas_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VEGAS_B300_VEGAS_H */

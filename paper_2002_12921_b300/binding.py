@@ -1,0 +1,222 @@
+"""Thin Python binding of the C ABI in include/vegas.h (ctypes).
+
+Argument marshalling only: every step of the Vegas iteration runs in the CUDA
+library ``_build/libvegas_b300.so``.  The functions keep the C names.  If the
+library is missing, the first call raises -- there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libvegas_b300.so")
+
+VEGAS_OK, VEGAS_EINVAL, VEGAS_ECUDA, VEGAS_ENONFINITE, VEGAS_ESTATE, VEGAS_ENOSPACE = range(6)
+VEGAS_FP64, VEGAS_FP32_EVAL = 0, 1
+VEGAS_GAUSS, VEGAS_GAUSS_MIX2, VEGAS_FLAT, VEGAS_GENZ_DISC, VEGAS_GENZ_PPEAK = range(5)
+VEGAS_MAX_DIM, VEGAS_MAX_BINS, VEGAS_MAX_DIM_X_BINS = 16, 1024, 8192
+LOG_COLUMNS = ("S1", "S2", "n", "nonfinite", "I", "var")
+
+# every symbol include/vegas.h declares
+EXPORTED = ("vegas_workspace_bytes", "vegas_init_grid", "vegas_set_config", "vegas_iterate",
+            "vegas_refine", "vegas_result", "vegas_get_iterations", "vegas_get_grid",
+            "vegas_set_grid", "vegas_get_histogram", "vegas_sample_words", "vegas_destroy",
+            "vegas_strerror")
+
+
+class VegasError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {vegas_strerror(status)} (status {status})")
+
+
+class vegas_config(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("min_samples_per_thread", ctypes.c_int), ("chunk_samples", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library missing: {LIB_PATH} (run "
+                               "`python -m paper_2002_12921_b300.build`)")
+        L = ctypes.CDLL(LIB_PATH)
+        i32, u64, vp, dbl, sz = (ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_double,
+                                 ctypes.c_size_t)
+        ip = ctypes.POINTER(ctypes.c_int)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.vegas_workspace_bytes.argtypes = [i32, i32, i32, ctypes.POINTER(sz)]
+        L.vegas_init_grid.argtypes = [ctypes.POINTER(vp), i32, i32, u64, i32, i32, vp, i32, i32,
+                                      vp, sz, vp]
+        L.vegas_set_config.argtypes = [vp, ctypes.POINTER(vegas_config)]
+        L.vegas_iterate.argtypes = [vp, u64, i32]
+        L.vegas_refine.argtypes = [vp, dbl]
+        L.vegas_result.argtypes = [vp, i32, dp, dp, dp, ip]
+        L.vegas_get_iterations.argtypes = [vp, vp, i32, ip]
+        L.vegas_get_grid.argtypes = [vp, vp]
+        L.vegas_set_grid.argtypes = [vp, vp]
+        L.vegas_get_histogram.argtypes = [vp, vp]
+        L.vegas_sample_words.argtypes = [u64, ctypes.c_uint32, ctypes.c_uint32, u64, u64, i32, vp,
+                                         vp]
+        L.vegas_destroy.argtypes = [vp]
+        L.vegas_strerror.argtypes = [i32]
+        L.vegas_strerror.restype = ctypes.c_char_p
+        for name in EXPORTED:
+            if name != "vegas_strerror":
+                getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(rc, where):
+    if rc != VEGAS_OK:
+        raise VegasError(rc, where)
+
+
+def vegas_strerror(status):
+    return lib().vegas_strerror(int(status)).decode()
+
+
+def vegas_workspace_bytes(dim, nbins, max_iters):
+    out = ctypes.c_size_t(0)
+    _check(lib().vegas_workspace_bytes(dim, nbins, max_iters, ctypes.byref(out)),
+           "vegas_workspace_bytes")
+    return out.value
+
+
+def vegas_init_grid(dim, nbins, seed, mode, integrand, params, max_iters, d_workspace, ws_bytes,
+                    cuda_stream):
+    """Returns the opaque handle (an int)."""
+    p = np.ascontiguousarray(params if params is not None else [], dtype=np.float64)
+    h = ctypes.c_void_p(None)
+    _check(lib().vegas_init_grid(ctypes.byref(h), dim, nbins, seed & (2**64 - 1), mode, integrand,
+                                 p.ctypes.data if p.size else None, int(p.size), max_iters,
+                                 d_workspace, ws_bytes, cuda_stream), "vegas_init_grid")
+    return h.value
+
+
+def vegas_set_config(h, block_threads=0, blocks_per_sm=0, min_samples_per_thread=0,
+                     chunk_samples=0):
+    cfg = vegas_config(block_threads, blocks_per_sm, min_samples_per_thread, chunk_samples)
+    _check(lib().vegas_set_config(h, ctypes.byref(cfg)), "vegas_set_config")
+
+
+def vegas_iterate(h, n_samples, adapt):
+    _check(lib().vegas_iterate(h, int(n_samples), 1 if adapt else 0), "vegas_iterate")
+
+
+def vegas_refine(h, alpha):
+    _check(lib().vegas_refine(h, float(alpha)), "vegas_refine")
+
+
+def vegas_result(h, first_iter=0):
+    """(mean, sigma, chi2_dof, n_iter, nonfinite_seen)."""
+    m, s, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    n = ctypes.c_int()
+    rc = lib().vegas_result(h, first_iter, ctypes.byref(m), ctypes.byref(s), ctypes.byref(c),
+                            ctypes.byref(n))
+    if rc not in (VEGAS_OK, VEGAS_ENONFINITE):
+        raise VegasError(rc, "vegas_result")
+    return m.value, s.value, c.value, n.value, rc == VEGAS_ENONFINITE
+
+
+def vegas_get_iterations(h, max_rows=1 << 16):
+    rows = np.zeros((max_rows, 6))
+    n = ctypes.c_int()
+    _check(lib().vegas_get_iterations(h, rows.ctypes.data, max_rows, ctypes.byref(n)),
+           "vegas_get_iterations")
+    return rows[: n.value].copy()
+
+
+def vegas_get_grid(h, dim, nbins):
+    e = np.empty((dim, nbins + 1))
+    _check(lib().vegas_get_grid(h, e.ctypes.data), "vegas_get_grid")
+    return e
+
+
+def vegas_set_grid(h, edges):
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    _check(lib().vegas_set_grid(h, e.ctypes.data), "vegas_set_grid")
+
+
+def vegas_get_histogram(h, dim, nbins):
+    out = np.empty((dim, nbins))
+    _check(lib().vegas_get_histogram(h, out.ctypes.data), "vegas_get_histogram")
+    return out
+
+
+def vegas_sample_words(seed, integral_id, it, i0, n, dim, d_out, cuda_stream):
+    """Philox words of samples i0 .. i0+n-1 into the device buffer d_out (n x dim uint32)."""
+    _check(lib().vegas_sample_words(seed & (2**64 - 1), integral_id, it, i0, n, dim, d_out,
+                                    cuda_stream), "vegas_sample_words")
+
+
+def vegas_destroy(h):
+    if h:
+        _check(lib().vegas_destroy(h), "vegas_destroy")
+
+
+class Vegas:
+    """One integration state on a CUDA device: torch owns the workspace and
+    supplies the stream; the library does all the work."""
+
+    def __init__(self, dim, nbins, seed, mode, integrand, params, max_iters=64, device="cuda",
+                 stream=None):
+        import torch
+
+        self.dim, self.nbins = dim, nbins
+        self.ws_bytes = vegas_workspace_bytes(dim, nbins, max_iters)
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.workspace.device)
+        self.handle = vegas_init_grid(dim, nbins, seed, mode, integrand, params, max_iters,
+                                      self.workspace.data_ptr(), self.ws_bytes,
+                                      self.stream.cuda_stream)
+
+    def config(self, **kw):
+        vegas_set_config(self.handle, **kw)
+
+    def iterate(self, n, adapt):
+        vegas_iterate(self.handle, n, adapt)
+
+    def refine(self, alpha=1.5):
+        vegas_refine(self.handle, alpha)
+
+    def result(self, first_iter=0):
+        return vegas_result(self.handle, first_iter)
+
+    def iterations(self):
+        return vegas_get_iterations(self.handle)
+
+    def grid(self):
+        return vegas_get_grid(self.handle, self.dim, self.nbins)
+
+    def set_grid(self, edges):
+        vegas_set_grid(self.handle, edges)
+
+    def histogram(self):
+        return vegas_get_histogram(self.handle, self.dim, self.nbins)
+
+    def run(self, schedule, alpha=1.5):
+        """Enqueue (n, adapt) iterations; each adapting one is followed by a
+        refinement.  Asynchronous."""
+        for n, adapt in schedule:
+            self.iterate(n, adapt)
+            if adapt:
+                self.refine(alpha)
+
+    def close(self):
+        if self.handle:
+            vegas_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,440 @@
+// The fused Vegas iteration kernel: Philox4x32-10 -> grid map -> integrand ->
+// per-thread sums -> block reduction -> privatised shared-memory histogram with
+// one global flush per block -> last-block fixed-order tail reduction into the
+// device iteration log.
+//
+// Method: VegasFlow Sec. 2.2 (the per-event step of the importance-sampling
+// integrator) with the Vegas map and estimator of Lepage 1978 (cited in Sec. 1):
+// for each sample, y in [0,1)^d picks bin j_k and a position inside it in every
+// dimension, x_k = e_{k,j} + frac (e_{k,j+1} - e_{k,j}), the weight is
+// J = prod_k N (e_{k,j+1} - e_{k,j}), and the iteration estimates I = <f J>,
+// var = (<(fJ)^2> - I^2)/(n-1), while accumulating sum (fJ)^2 per (k, j_k) for
+// the refinement.
+//
+// Two precisions share the structure:
+//   double: map, integrand and all sums in double ("plain FP64");
+//   float:  map and integrand in float; every thread keeps Kahan-compensated
+//           float sums of f J and (f J)^2 and a float shared histogram, all
+//           pre-scaled by 2^-h (h from the previous iteration's estimate) so
+//           that no float sum overflows; everything above the thread is double.
+#pragma once
+
+#include <cfloat>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "philox.cuh"
+#include "vegas_internal.h"
+
+namespace vegas {
+
+// ------------------------------------------------------------------------
+// Integrands.  begin() resets the running state, add(k, x) folds in
+// dimension k (a compile-time constant once the kernel's loops are unrolled,
+// so the constants come straight from the parameter bank), value() returns f
+// without its constant prefactor (which the kernel folds into the Jacobian).
+// ------------------------------------------------------------------------
+template <typename R, int FN>
+struct Integrand;
+
+// Eq. 1, float: s = sum_k ((x_k - mu_k) kappa)^2 with kappa^2 = log2(e)/a^2, f ~ 2^-s.
+template <>
+struct Integrand<float, VEGAS_GAUSS> {
+    float s;
+    __device__ __forceinline__ void begin() { s = 0.f; }
+    __device__ __forceinline__ void add(int k, float x, const FnConsts& c) {
+        const float u = fmaf(x, c.kappa, c.q0[k]);
+        s = fmaf(u, u, s);
+    }
+    __device__ __forceinline__ float value(const FnConsts&) const { return exp2f(-s); }
+};
+
+template <>
+struct Integrand<float, VEGAS_GAUSS_MIX2> {
+    float sa, sb;
+    __device__ __forceinline__ void begin() { sa = 0.f; sb = 0.f; }
+    __device__ __forceinline__ void add(int k, float x, const FnConsts& c) {
+        const float ua = fmaf(x, c.kappa, c.q0[k]);
+        const float ub = fmaf(x, c.kappa, c.q1[k]);
+        sa = fmaf(ua, ua, sa);
+        sb = fmaf(ub, ub, sb);
+    }
+    __device__ __forceinline__ float value(const FnConsts&) const {
+        return exp2f(-sa) + exp2f(-sb);
+    }
+};
+
+template <>
+struct Integrand<float, VEGAS_FLAT> {
+    __device__ __forceinline__ void begin() {}
+    __device__ __forceinline__ void add(int, float, const FnConsts&) {}
+    __device__ __forceinline__ float value(const FnConsts&) const { return 1.f; }
+};
+
+// Eq. 2, float: q0 = a_k (threshold), q1 = c_k log2(e).
+template <>
+struct Integrand<float, VEGAS_GENZ_DISC> {
+    float s;
+    bool inside;
+    __device__ __forceinline__ void begin() { s = 0.f; inside = true; }
+    __device__ __forceinline__ void add(int k, float x, const FnConsts& c) {
+        s = fmaf(x, c.q1[k], s);
+        inside = inside && (x > c.q0[k]);
+    }
+    __device__ __forceinline__ float value(const FnConsts&) const {
+        return inside ? exp2f(s) : 0.f;
+    }
+};
+
+// Eq. 3, float: 1/(c^-2 + u^2) = c^2 / (1 + (c u)^2); q1 = c_k, q0 = -a_k c_k;
+// the c_k^2 and the normalisation sit in the prefactor.
+template <>
+struct Integrand<float, VEGAS_GENZ_PPEAK> {
+    float p;
+    __device__ __forceinline__ void begin() { p = 1.f; }
+    __device__ __forceinline__ void add(int k, float x, const FnConsts& c) {
+        const float t = fmaf(x, c.q1[k], c.q0[k]);
+        p *= fmaf(t, t, 1.f);
+    }
+    __device__ __forceinline__ float value(const FnConsts&) const { return __fdividef(1.f, p); }
+};
+
+// Eq. 1, double: exp(-sum (x_k - mu_k)^2 / a^2).
+template <>
+struct Integrand<double, VEGAS_GAUSS> {
+    double s;
+    __device__ __forceinline__ void begin() { s = 0.0; }
+    __device__ __forceinline__ void add(int k, double x, const FnConsts& c) {
+        const double u = x - c.p0[k];
+        s = fma(u, u, s);
+    }
+    __device__ __forceinline__ double value(const FnConsts& c) const { return exp(-s * c.inv_a2); }
+};
+
+template <>
+struct Integrand<double, VEGAS_GAUSS_MIX2> {
+    double sa, sb;
+    __device__ __forceinline__ void begin() { sa = 0.0; sb = 0.0; }
+    __device__ __forceinline__ void add(int k, double x, const FnConsts& c) {
+        const double ua = x - c.p0[k];
+        const double ub = x - c.p1[k];
+        sa = fma(ua, ua, sa);
+        sb = fma(ub, ub, sb);
+    }
+    __device__ __forceinline__ double value(const FnConsts& c) const {
+        return exp(-sa * c.inv_a2) + exp(-sb * c.inv_a2);
+    }
+};
+
+template <>
+struct Integrand<double, VEGAS_FLAT> {
+    __device__ __forceinline__ void begin() {}
+    __device__ __forceinline__ void add(int, double, const FnConsts&) {}
+    __device__ __forceinline__ double value(const FnConsts&) const { return 1.0; }
+};
+
+// Eq. 2, double: p0 = a_k, p1 = c_k.
+template <>
+struct Integrand<double, VEGAS_GENZ_DISC> {
+    double s;
+    bool inside;
+    __device__ __forceinline__ void begin() { s = 0.0; inside = true; }
+    __device__ __forceinline__ void add(int k, double x, const FnConsts& c) {
+        s = fma(c.p1[k], x, s);
+        inside = inside && (x > c.p0[k]);
+    }
+    __device__ __forceinline__ double value(const FnConsts&) const {
+        return inside ? exp(s) : 0.0;
+    }
+};
+
+// Eq. 3, double: p0 = a_k, p1 = c_k^-2; f ~ 1 / prod_k (c_k^-2 + (x_k - a_k)^2).
+template <>
+struct Integrand<double, VEGAS_GENZ_PPEAK> {
+    double p;
+    __device__ __forceinline__ void begin() { p = 1.0; }
+    __device__ __forceinline__ void add(int k, double x, const FnConsts& c) {
+        const double u = x - c.p0[k];
+        p *= fma(u, u, c.p1[k]);
+    }
+    __device__ __forceinline__ double value(const FnConsts&) const { return 1.0 / p; }
+};
+
+// ------------------------------------------------------------------------
+// Precision-specific pieces of the map.
+// ------------------------------------------------------------------------
+template <typename R>
+struct Prec;
+
+template <>
+struct Prec<float> {
+    using Pair = float2;  // (edge, width) of one bin, in shared memory
+    using Hist = float;
+    // frac = (floor(l / 2^9) + 1/2) 2^-23: the float in [1, 2) with those 23
+    // mantissa bits, minus (1 - 2^-24); both steps are exact.
+    static __device__ __forceinline__ float frac(uint32_t l) {
+        return __uint_as_float(0x3F800000u | (l >> 9)) - 0x1.fffffep-1f;
+    }
+    static __device__ __forceinline__ Pair pair(double e0, double e1) {
+        const float f0 = (float)e0, f1 = (float)e1;
+        return make_float2(f0, f1 - f0);
+    }
+    static __device__ __forceinline__ bool finite(float v) { return fabsf(v) <= FLT_MAX; }
+    static __device__ __forceinline__ float fma(float x, float y, float z) { return fmaf(x, y, z); }
+};
+
+template <>
+struct Prec<double> {
+    using Pair = double2;
+    using Hist = double;
+    // frac = (l + 1/2) 2^-32: the double 1 + l 2^-32, minus (1 - 2^-33); exact.
+    static __device__ __forceinline__ double frac(uint32_t l) {
+        return __hiloint2double((int)(0x3FF00000u | (l >> 12)), (int)(l << 20)) -
+               0x1.ffffffffp-1;
+    }
+    static __device__ __forceinline__ Pair pair(double e0, double e1) {
+        return make_double2(e0, e1 - e0);
+    }
+    static __device__ __forceinline__ bool finite(double v) { return fabs(v) <= DBL_MAX; }
+    static __device__ __forceinline__ double fma(double x, double y, double z) {
+        return ::fma(x, y, z);
+    }
+};
+
+// Sum over the block in a fixed order (shuffle tree, then warp 0); the result
+// is valid in thread 0.  sbuf holds 32 values.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sbuf) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sbuf[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = ((int)threadIdx.x < nw) ? sbuf[threadIdx.x] : T(0);
+    if (wid == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+// Per-thread accumulators: compensated in float, plain in double.
+template <typename R>
+struct Acc;
+
+template <>
+struct Acc<float> {
+    float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
+    // Kahan: c carries what the last addition rounded away (with its sign
+    // flipped), and is taken off the next term.
+    __device__ __forceinline__ void add(float v) {
+        const float y1 = v - c1;
+        const float t1 = s1 + y1;
+        c1 = (t1 - s1) - y1;
+        s1 = t1;
+        const float v2 = __fmul_rn(v, v);
+        const float y2 = v2 - c2;
+        const float t2 = s2 + y2;
+        c2 = (t2 - s2) - y2;
+        s2 = t2;
+    }
+    __device__ __forceinline__ double sum1() const { return (double)s1 - (double)c1; }
+    __device__ __forceinline__ double sum2() const { return (double)s2 - (double)c2; }
+};
+
+template <>
+struct Acc<double> {
+    double s1 = 0.0, s2 = 0.0;
+    __device__ __forceinline__ void add(double v) {
+        s1 += v;
+        s2 = fma(v, v, s2);
+    }
+    __device__ __forceinline__ double sum1() const { return s1; }
+    __device__ __forceinline__ double sum2() const { return s2; }
+};
+
+// ------------------------------------------------------------------------
+// The kernel.  R = float or double, D = dimension, FN = integrand id, ADAPT =
+// accumulate the refinement histogram.
+// ------------------------------------------------------------------------
+template <typename R, int D, int FN, bool ADAPT>
+__global__ void __launch_bounds__(256) vegas_iterate_kernel(const IterArgs a) {
+    using P = Prec<R>;
+    using Pair = typename P::Pair;
+    using H = typename P::Hist;
+    constexpr int DC = (D + 3) / 4;  // Philox calls per sample
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double sred[32];
+    __shared__ unsigned sbad[32];
+    __shared__ int s_last;
+
+    const int N = a.nbins;
+    Pair* sgrid = reinterpret_cast<Pair*>(smem_raw);
+    H* shist = reinterpret_cast<H*>(sgrid + D * N);
+
+    const unsigned it = a.ctrl[kIter];
+    if (it >= (unsigned)a.max_iters) {  // log full: the host refuses this too
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctrl[kStatus], kStatusLogFull);
+        return;
+    }
+
+    // Stage the grid as (edge, width) pairs; clear the block's histogram.
+    for (int idx = threadIdx.x; idx < D * N; idx += blockDim.x) {
+        const int k = idx / N, j = idx - k * N;
+        const double* e = a.edges + (size_t)k * (N + 1) + j;
+        sgrid[idx] = P::pair(e[0], e[1]);
+        if (ADAPT) shist[idx] = H(0);
+    }
+
+    // Pre-scale of the float path: f J is carried as f J 2^-h with 2^h near the
+    // previous iteration's estimate; the prefactor enters the Jacobian's start.
+    int h = 0;
+    double j0;
+    if (sizeof(R) == 4) {
+        if (it > 0) {
+            const double prev = a.log[(size_t)(it - 1) * kLogStride + 4];
+            if (prev > 0.0 && prev <= DBL_MAX) h = max(-120, min(120, ilogb(prev)));
+        }
+        j0 = ldexp(a.fc.C32, -h);
+    } else {
+        j0 = a.fc.C;
+    }
+    const R jstart = (R)j0;
+    // float: the factor N^D enters once per Philox group of four dimensions
+    const R n4 = (R)((double)N * N * N * N);
+    double nrem = 1.0;
+    for (int r = 0; r < D % 4; ++r) nrem *= N;
+    const R nlast = (R)nrem;
+    __syncthreads();
+
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long end = a.i0 + a.n_chunk;
+    const uint32_t c2base = a.integral_id << 8;
+
+    Acc<R> acc;
+    unsigned bad = 0;
+
+    for (unsigned long long i = a.i0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+         i < end; i += stride) {
+        Integrand<R, FN> f;
+        f.begin();
+        R J = jstart;
+        int hb[D];
+#pragma unroll
+        for (int q = 0; q < DC; ++q) {
+            uint32_t w0 = (uint32_t)i, w1 = (uint32_t)(i >> 32), w2 = c2base | (uint32_t)q, w3 = it;
+            philox4x32_10(w0, w1, w2, w3, a.rk0, a.rk1);
+            const uint32_t w[4] = {w0, w1, w2, w3};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int k = 4 * q + t;
+                if (k < D) {
+                    const uint32_t j = __umulhi(w[t], (uint32_t)N);
+                    const uint32_t l = w[t] * (uint32_t)N;
+                    const Pair g = sgrid[k * N + j];
+                    const R x = P::fma(P::frac(l), g.y, g.x);
+                    J *= g.y;
+                    f.add(k, x, a.fc);
+                    if (ADAPT) hb[k] = k * N + (int)j;
+                }
+            }
+            if (sizeof(R) == 4) J *= (4 * q + 4 <= D) ? n4 : nlast;
+        }
+        const R fw = f.value(a.fc) * J;
+        if (P::finite(fw)) {
+            acc.add(fw);
+            if (ADAPT) {
+                const R fw2 = fw * fw;
+#pragma unroll
+                for (int k = 0; k < D; ++k) atomicAdd(&shist[hb[k]], (H)fw2);
+            }
+        } else {
+            ++bad;
+        }
+    }
+
+    // Block reduction of the sums (fixed order), scaled back by 2^h / 2^2h.
+    const double sc1 = ldexp(1.0, h), sc2 = ldexp(1.0, 2 * h);
+    const double b1 = block_sum(acc.sum1(), sred);
+    const double b2 = block_sum(acc.sum2(), sred);
+    const unsigned bb = block_sum(bad, sbad);
+
+    // Flush the block's histogram: one global atomic per non-empty bin.
+    if (ADAPT) {
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < D * N; idx += blockDim.x) {
+            const H v = shist[idx];
+            if (v != H(0)) atomicAdd(&a.hist[idx], (double)v * sc2);
+        }
+    }
+
+    // Publish the block partial; the last block to finish reduces them all in
+    // block order and appends the iteration to the log.
+    if (threadIdx.x == 0) {
+        double* p = a.partials + (size_t)blockIdx.x * kPartialStride;
+        p[0] = b1 * sc1;
+        p[1] = b2 * sc2;
+        p[2] = (double)bb;
+        __threadfence();
+        const unsigned ticket = atomicAdd(&a.ctrl[kTicket], 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+
+    double t1 = 0.0, t2 = 0.0, tb = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        const double* p = a.partials + (size_t)b * kPartialStride;
+        t1 += __ldcg(p + 0);
+        t2 += __ldcg(p + 1);
+        tb += __ldcg(p + 2);
+    }
+    t1 = block_sum(t1, sred);
+    t2 = block_sum(t2, sred);
+    tb = block_sum(tb, sred);
+    if (threadIdx.x == 0) {
+        double* L = a.log + (size_t)it * kLogStride;
+        if (a.first_chunk) {
+            L[0] = t1; L[1] = t2; L[2] = (double)a.n_chunk; L[3] = tb;
+        } else {
+            L[0] += t1; L[1] += t2; L[2] += (double)a.n_chunk; L[3] += tb;
+        }
+        if (a.last_chunk) {
+            const double n = (double)a.n_total;
+            const double I = L[0] / n;
+            const double var = (L[1] / n - I * I) / (n - 1.0);
+            L[4] = I;
+            L[5] = var > 0.0 ? var : 0.0;
+            L[6] = 0.0;
+            L[7] = 0.0;
+            a.ctrl[kIter] = it + 1;
+        }
+        a.ctrl[kTicket] = 0u;
+    }
+}
+
+}  // namespace vegas
+
+// Kernel table of one (precision, integrand): index [dim - 1][adapt].
+#define VEGAS_KERNEL_ROW(R, FN, D) \
+    {(const void*)&vegas::vegas_iterate_kernel<R, D, FN, false>, \
+     (const void*)&vegas::vegas_iterate_kernel<R, D, FN, true>}
+
+#define VEGAS_KERNEL_TABLE(name, R, FN)                                                       \
+    namespace vegas {                                                                         \
+    const void* name(int dim, bool adapt) {                                                   \
+        static const void* const table[kMaxDim][2] = {                                        \
+            VEGAS_KERNEL_ROW(R, FN, 1),  VEGAS_KERNEL_ROW(R, FN, 2),  VEGAS_KERNEL_ROW(R, FN, 3),  \
+            VEGAS_KERNEL_ROW(R, FN, 4),  VEGAS_KERNEL_ROW(R, FN, 5),  VEGAS_KERNEL_ROW(R, FN, 6),  \
+            VEGAS_KERNEL_ROW(R, FN, 7),  VEGAS_KERNEL_ROW(R, FN, 8),  VEGAS_KERNEL_ROW(R, FN, 9),  \
+            VEGAS_KERNEL_ROW(R, FN, 10), VEGAS_KERNEL_ROW(R, FN, 11), VEGAS_KERNEL_ROW(R, FN, 12), \
+            VEGAS_KERNEL_ROW(R, FN, 13), VEGAS_KERNEL_ROW(R, FN, 14), VEGAS_KERNEL_ROW(R, FN, 15), \
+            VEGAS_KERNEL_ROW(R, FN, 16)};                                                     \
+        if (dim < 1 || dim > kMaxDim) return nullptr;                                         \
+        return table[dim - 1][adapt ? 1 : 0];                                                 \
+    }                                                                                         \
+    }

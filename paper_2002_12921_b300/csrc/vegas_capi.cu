@@ -1,0 +1,538 @@
+// Host side of the C ABI declared in include/vegas.h: argument checks,
+// workspace layout, integrand constants, launch configuration, and the
+// host-side combination of iterations.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "philox.cuh"
+#include "vegas_internal.h"
+
+namespace vegas {
+const void* iterate_table_f32_gauss(int dim, bool adapt);
+const void* iterate_table_f32_mix2(int dim, bool adapt);
+const void* iterate_table_f32_flat(int dim, bool adapt);
+const void* iterate_table_f32_genz_disc(int dim, bool adapt);
+const void* iterate_table_f32_genz_ppeak(int dim, bool adapt);
+const void* iterate_table_f64_gauss(int dim, bool adapt);
+const void* iterate_table_f64_mix2(int dim, bool adapt);
+const void* iterate_table_f64_flat(int dim, bool adapt);
+const void* iterate_table_f64_genz_disc(int dim, bool adapt);
+const void* iterate_table_f64_genz_ppeak(int dim, bool adapt);
+
+const void* iterate_kernel_f32(int integrand, int dim, bool adapt) {
+    switch (integrand) {
+    case VEGAS_GAUSS: return iterate_table_f32_gauss(dim, adapt);
+    case VEGAS_GAUSS_MIX2: return iterate_table_f32_mix2(dim, adapt);
+    case VEGAS_FLAT: return iterate_table_f32_flat(dim, adapt);
+    case VEGAS_GENZ_DISC: return iterate_table_f32_genz_disc(dim, adapt);
+    case VEGAS_GENZ_PPEAK: return iterate_table_f32_genz_ppeak(dim, adapt);
+    default: return nullptr;
+    }
+}
+
+const void* iterate_kernel_f64(int integrand, int dim, bool adapt) {
+    switch (integrand) {
+    case VEGAS_GAUSS: return iterate_table_f64_gauss(dim, adapt);
+    case VEGAS_GAUSS_MIX2: return iterate_table_f64_mix2(dim, adapt);
+    case VEGAS_FLAT: return iterate_table_f64_flat(dim, adapt);
+    case VEGAS_GENZ_DISC: return iterate_table_f64_genz_disc(dim, adapt);
+    case VEGAS_GENZ_PPEAK: return iterate_table_f64_genz_ppeak(dim, adapt);
+    default: return nullptr;
+    }
+}
+
+size_t iterate_smem_bytes(int mode, int dim, int nbins, bool adapt) {
+    const size_t pair = mode == VEGAS_FP32_EVAL ? 2 * sizeof(float) : 2 * sizeof(double);
+    const size_t hist = mode == VEGAS_FP32_EVAL ? sizeof(float) : sizeof(double);
+    return (size_t)dim * nbins * (pair + (adapt ? hist : 0));
+}
+}  // namespace vegas
+
+using namespace vegas;
+
+struct vegas_state {
+    int dim, nbins, mode, integrand, max_iters;
+    uint64_t seed;
+    cudaStream_t stream;
+    int device;
+    int sm_count;
+    unsigned char* ws;
+    size_t ws_bytes;
+    double* edges;
+    double* hist;
+    double* log;
+    double* partials;
+    unsigned* ctrl;
+    int host_iters;  // iterations enqueued through this descriptor
+    vegas_config cfg;
+    FnConsts fc;
+    uint32_t rk0[10], rk1[10];
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+    size_t edges, hist, log, partials, ctrl, total;
+};
+
+Layout layout(int dim, int nbins, int max_iters) {
+    Layout L;
+    size_t off = 0;
+    L.edges = off;
+    off = align_up(off + (size_t)dim * (nbins + 1) * sizeof(double));
+    L.hist = off;
+    off = align_up(off + (size_t)dim * nbins * sizeof(double));
+    L.log = off;
+    off = align_up(off + (size_t)max_iters * kLogStride * sizeof(double));
+    L.partials = off;
+    off = align_up(off + (size_t)kMaxGrid * kPartialStride * sizeof(double));
+    L.ctrl = off;
+    off = align_up(off + kCtrlWords * sizeof(unsigned));
+    L.total = off;
+    return L;
+}
+
+bool shape_ok(int dim, int nbins, int max_iters) {
+    return dim >= 1 && dim <= kMaxDim && nbins >= 1 && nbins <= kMaxBins &&
+           dim * nbins <= kMaxDimBins && max_iters >= 1 && max_iters <= (1 << 24);
+}
+
+// Current-device guard: every call runs on the device that holds the workspace.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool finite_all(const double* p, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+// Integrand constants for both precisions (see FnConsts).
+int make_consts(int integrand, int dim, int nbins, const double* params, int nparams,
+                FnConsts* fc) {
+    std::memset(fc, 0, sizeof(*fc));
+    const double log2e = 1.4426950408889634;
+    const double npow = std::pow((double)nbins, dim);  // N^dim of the FP64 Jacobian
+    switch (integrand) {
+    case VEGAS_GAUSS:
+    case VEGAS_GAUSS_MIX2: {
+        const int need = integrand == VEGAS_GAUSS ? 1 + dim : 1 + 2 * dim;
+        if (!params || nparams < need || !finite_all(params, need)) return VEGAS_EINVAL;
+        const double a = params[0];
+        if (!(a > 0.0)) return VEGAS_EINVAL;
+        // (a sqrt(pi))^-d, halved for the two-term mixture
+        double norm = std::pow(a * std::sqrt(M_PI), -(double)dim);
+        if (integrand == VEGAS_GAUSS_MIX2) norm *= 0.5;
+        fc->C = norm * npow;
+        fc->C32 = norm;
+        fc->inv_a2 = 1.0 / (a * a);
+        const double kappa = std::sqrt(log2e) / a;
+        fc->kappa = (float)kappa;
+        for (int k = 0; k < dim; ++k) {
+            fc->p0[k] = params[1 + k];
+            fc->q0[k] = (float)(-params[1 + k] * kappa);
+            if (integrand == VEGAS_GAUSS_MIX2) {
+                fc->p1[k] = params[1 + dim + k];
+                fc->q1[k] = (float)(-params[1 + dim + k] * kappa);
+            }
+        }
+        return VEGAS_OK;
+    }
+    case VEGAS_FLAT:
+        fc->C = npow;
+        fc->C32 = 1.0;
+        return VEGAS_OK;
+    case VEGAS_GENZ_DISC: {
+        if (!params || nparams < 2 * dim || !finite_all(params, 2 * dim)) return VEGAS_EINVAL;
+        double norm = 1.0;  // prod_k (e^{c_k} - e^{c_k a_k}) / c_k
+        for (int k = 0; k < dim; ++k) {
+            const double ak = params[k], ck = params[dim + k];
+            if (ck == 0.0) return VEGAS_EINVAL;
+            norm *= (std::exp(ck) - std::exp(ck * ak)) / ck;
+            fc->p0[k] = ak;
+            fc->p1[k] = ck;
+            fc->q0[k] = (float)ak;
+            fc->q1[k] = (float)(ck * log2e);
+        }
+        if (!(norm > 0.0) || !std::isfinite(norm)) return VEGAS_EINVAL;
+        fc->C = npow / norm;
+        fc->C32 = 1.0 / norm;
+        return VEGAS_OK;
+    }
+    case VEGAS_GENZ_PPEAK: {
+        if (!params || nparams < 2 * dim || !finite_all(params, 2 * dim)) return VEGAS_EINVAL;
+        double inv_int = 1.0;   // prod_k 1/(c_k (atan(c_k (1-a_k)) + atan(c_k a_k)))
+        double c2 = 1.0;        // prod_k c_k^2
+        for (int k = 0; k < dim; ++k) {
+            const double ak = params[k], ck = params[dim + k];
+            if (!(ck > 0.0)) return VEGAS_EINVAL;
+            inv_int /= ck * (std::atan(ck * (1.0 - ak)) + std::atan(ck * ak));
+            c2 *= ck * ck;
+            fc->p0[k] = ak;
+            fc->p1[k] = 1.0 / (ck * ck);
+            fc->q0[k] = (float)(-ak * ck);
+            fc->q1[k] = (float)ck;
+        }
+        fc->C = inv_int * npow;
+        fc->C32 = inv_int * c2;
+        return VEGAS_OK;
+    }
+    default:
+        return VEGAS_EINVAL;
+    }
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? VEGAS_OK : VEGAS_ECUDA; }
+
+const void* kernel_for(const vegas_state* s, bool adapt) {
+    return s->mode == VEGAS_FP32_EVAL ? iterate_kernel_f32(s->integrand, s->dim, adapt)
+                                      : iterate_kernel_f64(s->integrand, s->dim, adapt);
+}
+
+void default_config(vegas_config* c) {
+    c->block_threads = 256;
+    c->blocks_per_sm = 0;
+    c->min_samples_per_thread = 8;
+    c->chunk_samples = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vegas_workspace_bytes(int dim, int nbins, int max_iters, size_t* bytes) {
+    if (!bytes || !shape_ok(dim, nbins, max_iters)) return VEGAS_EINVAL;
+    *bytes = layout(dim, nbins, max_iters).total;
+    return VEGAS_OK;
+}
+
+int vegas_init_grid(vegas_state** out, int dim, int nbins, uint64_t seed, int mode, int integrand,
+                    const double* params, int nparams, int max_iters, void* d_workspace,
+                    size_t ws_bytes, void* cuda_stream) {
+    if (!out) return VEGAS_EINVAL;
+    *out = nullptr;
+    if (!shape_ok(dim, nbins, max_iters) || !d_workspace) return VEGAS_EINVAL;
+    if (mode != VEGAS_FP64 && mode != VEGAS_FP32_EVAL) return VEGAS_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_workspace) % kAlign) != 0) return VEGAS_EINVAL;
+    const Layout L = layout(dim, nbins, max_iters);
+    if (ws_bytes < L.total) return VEGAS_ENOSPACE;
+
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, d_workspace) != cudaSuccess ||
+        attr.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return VEGAS_EINVAL;
+    }
+
+    vegas_state* s = new (std::nothrow) vegas_state;
+    if (!s) return VEGAS_EINVAL;
+    std::memset(s, 0, sizeof(*s));
+    s->dim = dim;
+    s->nbins = nbins;
+    s->mode = mode;
+    s->integrand = integrand;
+    s->max_iters = max_iters;
+    s->seed = seed;
+    s->stream = static_cast<cudaStream_t>(cuda_stream);
+    s->device = attr.device;
+    int rc = make_consts(integrand, dim, nbins, params, nparams, &s->fc);
+    if (rc != VEGAS_OK) { delete s; return rc; }
+    philox_round_keys(seed, s->rk0, s->rk1);
+    default_config(&s->cfg);
+
+    DeviceGuard g(s->device);
+    if (!g.ok) { delete s; return VEGAS_ECUDA; }
+    if (cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device) !=
+        cudaSuccess) {
+        delete s;
+        return VEGAS_ECUDA;
+    }
+    s->ws = static_cast<unsigned char*>(d_workspace);
+    s->ws_bytes = ws_bytes;
+    s->edges = reinterpret_cast<double*>(s->ws + L.edges);
+    s->hist = reinterpret_cast<double*>(s->ws + L.hist);
+    s->log = reinterpret_cast<double*>(s->ws + L.log);
+    s->partials = reinterpret_cast<double*>(s->ws + L.partials);
+    s->ctrl = reinterpret_cast<unsigned*>(s->ws + L.ctrl);
+
+    rc = cuda_status(launch_init(s->edges, s->hist, s->log, s->ctrl, dim, nbins, max_iters,
+                                 s->stream));
+    if (rc != VEGAS_OK) { delete s; return rc; }
+    *out = s;
+    return VEGAS_OK;
+}
+
+int vegas_set_config(vegas_state* s, const vegas_config* cfg) {
+    if (!s) return VEGAS_EINVAL;
+    vegas_config c;
+    default_config(&c);
+    if (cfg) {
+        if (cfg->block_threads) c.block_threads = cfg->block_threads;
+        if (cfg->blocks_per_sm) c.blocks_per_sm = cfg->blocks_per_sm;
+        if (cfg->min_samples_per_thread) c.min_samples_per_thread = cfg->min_samples_per_thread;
+        c.chunk_samples = cfg->chunk_samples;
+    }
+    if (c.block_threads < 32 || c.block_threads > 256 || c.block_threads % 32 != 0 ||
+        c.blocks_per_sm < 0 || c.blocks_per_sm > 64 || c.min_samples_per_thread < 1)
+        return VEGAS_EINVAL;
+    s->cfg = c;
+    return VEGAS_OK;
+}
+
+int vegas_iterate(vegas_state* s, uint64_t n_samples, int adapt) {
+    if (!s || n_samples < 2) return VEGAS_EINVAL;
+    if (s->host_iters >= s->max_iters) return VEGAS_ESTATE;
+    DeviceGuard g(s->device);
+    if (!g.ok) return VEGAS_ECUDA;
+
+    const bool ad = adapt != 0;
+    const void* kern = kernel_for(s, ad);
+    if (!kern) return VEGAS_EINVAL;
+    const size_t smem = iterate_smem_bytes(s->mode, s->dim, s->nbins, ad);
+    // static shared memory (~0.5 KB) counts against the 48 KB default as well
+    if (smem > 40 * 1024) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return VEGAS_ECUDA;
+    }
+    const int block = s->cfg.block_threads;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) != cudaSuccess ||
+        occ < 1)
+        return VEGAS_ECUDA;
+    const int bps = s->cfg.blocks_per_sm > 0 && s->cfg.blocks_per_sm < occ ? s->cfg.blocks_per_sm
+                                                                           : occ;
+    long long grid_max = (long long)s->sm_count * bps;
+    if (grid_max > kMaxGrid) grid_max = kMaxGrid;
+
+    // launches of at most 2^40 samples keep the grid-stride loop's index far
+    // from overflow; the user's chunk size splits further
+    uint64_t chunk = s->cfg.chunk_samples ? s->cfg.chunk_samples : n_samples;
+    const uint64_t kMaxChunk = 1ull << 40;
+    if (chunk > kMaxChunk) chunk = kMaxChunk;
+
+    IterArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.edges = s->edges;
+    a.hist = s->hist;
+    a.partials = s->partials;
+    a.log = s->log;
+    a.ctrl = s->ctrl;
+    a.n_total = n_samples;
+    a.nbins = s->nbins;
+    a.max_iters = s->max_iters;
+    a.integral_id = 0;
+    std::memcpy(a.rk0, s->rk0, sizeof(a.rk0));
+    std::memcpy(a.rk1, s->rk1, sizeof(a.rk1));
+    a.fc = s->fc;
+
+    for (uint64_t i0 = 0; i0 < n_samples; i0 += chunk) {
+        const uint64_t nc = (n_samples - i0) < chunk ? (n_samples - i0) : chunk;
+        a.i0 = i0;
+        a.n_chunk = nc;
+        a.first_chunk = i0 == 0;
+        a.last_chunk = i0 + nc == n_samples;
+        const uint64_t per_block = (uint64_t)block * s->cfg.min_samples_per_thread;
+        long long grid = (long long)((nc + per_block - 1) / per_block);
+        if (grid > grid_max) grid = grid_max;
+        if (grid < 1) grid = 1;
+        void* args[] = {&a};
+        const cudaError_t e =
+            cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(block), args, smem, s->stream);
+        if (e != cudaSuccess) return VEGAS_ECUDA;
+    }
+    s->host_iters++;
+    return VEGAS_OK;
+}
+
+int vegas_refine(vegas_state* s, double alpha) {
+    if (!s || !(alpha >= 0.0) || !std::isfinite(alpha)) return VEGAS_EINVAL;
+    DeviceGuard g(s->device);
+    if (!g.ok) return VEGAS_ECUDA;
+    RefineArgs r;
+    r.edges = s->edges;
+    r.hist = s->hist;
+    r.dim = s->dim;
+    r.nbins = s->nbins;
+    r.alpha = alpha;
+    return cuda_status(launch_refine(r, s->stream));
+}
+
+static int read_log(vegas_state* s, double* rows, int max_rows, int* n_rows, int* nonfinite_any,
+                    int first) {
+    unsigned ctrl[kCtrlWords];
+    if (cudaMemcpyAsync(ctrl, s->ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, s->stream) !=
+        cudaSuccess)
+        return VEGAS_ECUDA;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return VEGAS_ECUDA;
+    if (ctrl[kStatus] & kStatusLogFull) return VEGAS_ESTATE;
+    int n = (int)ctrl[kIter];
+    if (n > max_rows) n = max_rows;
+    if (n > 0) {
+        if (cudaMemcpyAsync(rows, s->log, (size_t)n * kLogStride * sizeof(double),
+                            cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+            return VEGAS_ECUDA;
+        if (cudaStreamSynchronize(s->stream) != cudaSuccess) return VEGAS_ECUDA;
+    }
+    *n_rows = n;
+    if (nonfinite_any) {
+        *nonfinite_any = 0;
+        for (int t = first; t < n; ++t)
+            if (rows[(size_t)t * kLogStride + 3] != 0.0) *nonfinite_any = 1;
+    }
+    return VEGAS_OK;
+}
+
+int vegas_result(vegas_state* s, int first_iter, double* mean, double* sigma, double* chi2_dof,
+                 int* n_iter) {
+    if (!s || first_iter < 0) return VEGAS_EINVAL;
+    DeviceGuard g(s->device);
+    if (!g.ok) return VEGAS_ECUDA;
+    double* rows = new (std::nothrow) double[(size_t)s->max_iters * kLogStride];
+    if (!rows) return VEGAS_EINVAL;
+    int n = 0, bad = 0;
+    int rc = read_log(s, rows, s->max_iters, &n, &bad, first_iter);
+    if (rc != VEGAS_OK) { delete[] rows; return rc; }
+    if (n_iter) *n_iter = n;
+    const int K = n - first_iter;
+    double m = NAN, sg = NAN, c2 = NAN;
+    if (K > 0) {
+        // inverse-variance weights; any zero-variance iteration: plain mean, sigma 0
+        bool zero = false;
+        for (int t = first_iter; t < n; ++t)
+            if (!(rows[(size_t)t * kLogStride + 5] > 0.0)) zero = true;
+        if (zero) {
+            double acc = 0.0;
+            for (int t = first_iter; t < n; ++t) acc += rows[(size_t)t * kLogStride + 4];
+            m = acc / K;
+            sg = 0.0;
+            double dev = 0.0;
+            for (int t = first_iter; t < n; ++t) {
+                const double d = rows[(size_t)t * kLogStride + 4] - m;
+                dev += d * d;
+            }
+            c2 = K > 1 ? (dev == 0.0 ? 0.0 : INFINITY) : 0.0;
+        } else {
+            double w = 0.0, wi = 0.0;
+            for (int t = first_iter; t < n; ++t) {
+                const double I = rows[(size_t)t * kLogStride + 4];
+                const double v = rows[(size_t)t * kLogStride + 5];
+                w += 1.0 / v;
+                wi += I / v;
+            }
+            m = wi / w;
+            sg = std::sqrt(1.0 / w);
+            double chi = 0.0;
+            for (int t = first_iter; t < n; ++t) {
+                const double d = rows[(size_t)t * kLogStride + 4] - m;
+                chi += d * d / rows[(size_t)t * kLogStride + 5];
+            }
+            c2 = K > 1 ? chi / (K - 1) : 0.0;
+        }
+    }
+    delete[] rows;
+    if (mean) *mean = m;
+    if (sigma) *sigma = sg;
+    if (chi2_dof) *chi2_dof = c2;
+    return bad ? VEGAS_ENONFINITE : VEGAS_OK;
+}
+
+int vegas_get_iterations(vegas_state* s, double* host_rows, int max_rows, int* n_rows) {
+    if (!s || !host_rows || max_rows < 0 || !n_rows) return VEGAS_EINVAL;
+    DeviceGuard g(s->device);
+    if (!g.ok) return VEGAS_ECUDA;
+    double* rows = new (std::nothrow) double[(size_t)s->max_iters * kLogStride];
+    if (!rows) return VEGAS_EINVAL;
+    int n = 0;
+    const int rc = read_log(s, rows, max_rows < s->max_iters ? max_rows : s->max_iters, &n,
+                            nullptr, 0);
+    if (rc == VEGAS_OK)
+        for (int t = 0; t < n; ++t)
+            for (int c = 0; c < 6; ++c)
+                host_rows[(size_t)t * 6 + c] = rows[(size_t)t * kLogStride + c];
+    *n_rows = rc == VEGAS_OK ? n : 0;
+    delete[] rows;
+    return rc;
+}
+
+int vegas_get_grid(vegas_state* s, double* host_edges) {
+    if (!s || !host_edges) return VEGAS_EINVAL;
+    DeviceGuard g(s->device);
+    if (!g.ok) return VEGAS_ECUDA;
+    const size_t bytes = (size_t)s->dim * (s->nbins + 1) * sizeof(double);
+    if (cudaMemcpyAsync(host_edges, s->edges, bytes, cudaMemcpyDeviceToHost, s->stream) !=
+        cudaSuccess)
+        return VEGAS_ECUDA;
+    return cuda_status(cudaStreamSynchronize(s->stream));
+}
+
+int vegas_set_grid(vegas_state* s, const double* host_edges) {
+    if (!s || !host_edges) return VEGAS_EINVAL;
+    const int N = s->nbins;
+    for (int k = 0; k < s->dim; ++k) {
+        const double* e = host_edges + (size_t)k * (N + 1);
+        if (e[0] != 0.0 || e[N] != 1.0) return VEGAS_ESTATE;
+        for (int l = 0; l < N; ++l)
+            if (!(e[l + 1] > e[l])) return VEGAS_ESTATE;
+    }
+    DeviceGuard g(s->device);
+    if (!g.ok) return VEGAS_ECUDA;
+    const size_t bytes = (size_t)s->dim * (N + 1) * sizeof(double);
+    if (cudaMemcpyAsync(s->edges, host_edges, bytes, cudaMemcpyHostToDevice, s->stream) !=
+        cudaSuccess)
+        return VEGAS_ECUDA;
+    return cuda_status(cudaStreamSynchronize(s->stream));
+}
+
+int vegas_get_histogram(vegas_state* s, double* host_hist) {
+    if (!s || !host_hist) return VEGAS_EINVAL;
+    DeviceGuard g(s->device);
+    if (!g.ok) return VEGAS_ECUDA;
+    const size_t bytes = (size_t)s->dim * s->nbins * sizeof(double);
+    if (cudaMemcpyAsync(host_hist, s->hist, bytes, cudaMemcpyDeviceToHost, s->stream) !=
+        cudaSuccess)
+        return VEGAS_ECUDA;
+    return cuda_status(cudaStreamSynchronize(s->stream));
+}
+
+int vegas_destroy(vegas_state* s) {
+    if (!s) return VEGAS_OK;
+    int rc = VEGAS_OK;
+    {
+        DeviceGuard g(s->device);
+        if (g.ok && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = VEGAS_ECUDA;
+    }
+    delete s;
+    return rc;
+}
+
+const char* vegas_strerror(int status) {
+    switch (status) {
+    case VEGAS_OK: return "ok";
+    case VEGAS_EINVAL: return "invalid argument";
+    case VEGAS_ECUDA: return "CUDA runtime error";
+    case VEGAS_ENONFINITE: return "non-finite integrand value (left out of the sums)";
+    case VEGAS_ESTATE: return "invalid state (call order, full iteration log or bad grid)";
+    case VEGAS_ENOSPACE: return "workspace too small";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

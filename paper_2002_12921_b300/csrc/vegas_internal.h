@@ -1,0 +1,74 @@
+// Internal declarations shared by the library's translation units (host and
+// device).  Not part of the public ABI (include/vegas.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vegas.h"
+
+namespace vegas {
+
+constexpr int kMaxDim = VEGAS_MAX_DIM;
+constexpr int kMaxBins = VEGAS_MAX_BINS;
+constexpr int kMaxDimBins = VEGAS_MAX_DIM_X_BINS;
+constexpr int kMaxGrid = 8192;      // blocks of one iterate launch (size of the partials array)
+constexpr int kPartialStride = 4;   // doubles per block partial: S1, S2, nonfinite, unused
+constexpr int kLogStride = 8;       // doubles per log row: S1, S2, n, nonfinite, I, var, 0, 0
+constexpr int kNumIntegrands = 5;
+
+// control words in device memory
+enum CtrlWord { kTicket = 0, kIter = 1, kStatus = 2, kCtrlWords = 64 };
+// status bits
+enum StatusBit { kStatusLogFull = 1u };
+
+// Integrand constants, precomputed on the host from the user's parameters.
+struct FnConsts {
+    // double-precision path
+    double C;        // prefactor: normalisation times N^dim (the FP64 Jacobian's N factors)
+    double inv_a2;   // GAUSS, MIX2: 1/a^2
+    double p0[kMaxDim];  // GAUSS, MIX2: centre A; GENZ: a_k
+    double p1[kMaxDim];  // MIX2: centre B; GENZ_DISC: c_k; GENZ_PPEAK: c_k^-2
+    // single-precision path (the prefactor C32 is applied in double per block)
+    double C32;      // prefactor for the FP32 path (without N^dim)
+    float kappa;     // GAUSS, MIX2: sqrt(log2 e)/a
+    float q0[kMaxDim];   // GAUSS, MIX2: -mu_A kappa; GENZ_DISC: a_k; GENZ_PPEAK: -a_k c_k
+    float q1[kMaxDim];   // MIX2: -mu_B kappa; GENZ_DISC: c_k log2 e; GENZ_PPEAK: c_k
+};
+
+// Arguments of one iterate launch (passed by value in the parameter bank).
+struct IterArgs {
+    const double* edges;  // dim x (N+1)
+    double* hist;         // dim x N
+    double* partials;     // gridDim.x x kPartialStride
+    double* log;          // max_iters x kLogStride
+    unsigned* ctrl;       // kCtrlWords
+    unsigned long long i0;       // first sample index of this launch
+    unsigned long long n_chunk;  // samples of this launch
+    unsigned long long n_total;  // samples of the whole iteration
+    int first_chunk, last_chunk;
+    int nbins, max_iters;
+    unsigned integral_id;
+    unsigned rk0[10], rk1[10];  // Philox round keys k + r W
+    FnConsts fc;
+};
+
+struct RefineArgs {
+    double* edges;  // dim x (N+1), refined in place
+    double* hist;   // dim x N, cleared
+    int dim, nbins;
+    double alpha;
+};
+
+// Kernel lookup: the iterate kernel for (mode, integrand, dim, adapt), or
+// nullptr.
+const void* iterate_kernel_f32(int integrand, int dim, bool adapt);
+const void* iterate_kernel_f64(int integrand, int dim, bool adapt);
+// dynamic shared memory of an iterate kernel
+size_t iterate_smem_bytes(int mode, int dim, int nbins, bool adapt);
+
+cudaError_t launch_refine(const RefineArgs& a, cudaStream_t stream);
+cudaError_t launch_init(double* edges, double* hist, double* log, unsigned* ctrl, int dim,
+                        int nbins, int max_iters, cudaStream_t stream);
+
+}  // namespace vegas

@@ -1,0 +1,67 @@
+"""The C-ABI library loads and exports every symbol include/vegas.h declares
+(CPU only: no call here reaches the GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2002_12921_b300 as V
+from paper_2002_12921_b300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "vegas.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^(?:const\s+)?\w+\s*\*?\s*(vegas_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return V.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(V.binding.EXPORTED)
+
+
+def test_workspace_bytes_validation(lib):
+    b = V.vegas_workspace_bytes(8, 50, 64)
+    assert b % 256 == 0 and b >= 8 * 51 * 8 + 8 * 50 * 8 + 64 * 8 * 8
+    assert V.vegas_workspace_bytes(16, 512, 1) > V.vegas_workspace_bytes(16, 100, 1)
+    for args in [(0, 50, 1), (17, 50, 1), (8, 0, 1), (8, 1025, 1), (16, 600, 1), (8, 50, 0)]:
+        with pytest.raises(V.VegasError) as e:
+            V.vegas_workspace_bytes(*args)
+        assert e.value.status == V.VEGAS_EINVAL
+
+
+def test_init_rejects_bad_arguments_before_touching_a_device(lib):
+    h = ctypes.c_void_p()
+    p = (ctypes.c_double * 5)(0.1, 0.5, 0.5, 0.5, 0.5)
+    ws = V.vegas_workspace_bytes(4, 50, 8)
+    # no workspace
+    assert lib.vegas_init_grid(ctypes.byref(h), 4, 50, 1, 0, 0, p, 5, 8, None, ws, None) == 1
+    # misaligned workspace pointer
+    assert lib.vegas_init_grid(ctypes.byref(h), 4, 50, 1, 0, 0, p, 5, 8, 0x1008, ws, None) == 1
+    # too small
+    assert lib.vegas_init_grid(ctypes.byref(h), 4, 50, 1, 0, 0, p, 5, 8, 0x10000, ws - 256,
+                               None) == V.VEGAS_ENOSPACE
+    # bad mode, bad shape
+    assert lib.vegas_init_grid(ctypes.byref(h), 4, 50, 1, 7, 0, p, 5, 8, 0x10000, ws, None) == 1
+    assert lib.vegas_init_grid(ctypes.byref(h), 40, 50, 1, 0, 0, p, 5, 8, 0x10000, ws, None) == 1
+    assert h.value is None
+    assert lib.vegas_destroy(None) == 0
+    assert lib.vegas_iterate(None, 100, 1) == 1
+    assert lib.vegas_sample_words(1, 0, 0, 0, 10, 0, None, None) == 1
+
+
+def test_strerror_covers_codes(lib):
+    texts = {V.vegas_strerror(c) for c in range(6)}
+    assert len(texts) == 6 and V.vegas_strerror(99) == "unknown status"

@@ -1,0 +1,232 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+FP64 mode: the same counters give the same samples, so per-iteration I, var,
+the histogram and the refined grid agree with the oracle to 1e-12 relative (the
+only differences are rounding order and 1-ulp differences of exp).
+FP32-eval mode: compared on the same grid and counters within the float
+error budget (|dI| <= 1e-5 |I|, |dvar| <= 1e-4 var for d <= 8; 3x that at
+d = 16), and statistically (3 sigma) over whole runs.
+"""
+import numpy as np
+import pytest
+from scipy.special import erf
+
+import oracle
+import paper_2002_12921_b300 as V
+from paper_2002_12921_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+RTOL64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    V.lib()
+
+
+def gpu_run(wl_dim, nbins, seed, fid, params, schedule, mode, alpha=1.5, edges=None, cfg=None,
+            max_iters=64, first_iter=0):
+    v = V.Vegas(wl_dim, nbins, seed, mode, fid, params, max_iters=max_iters)
+    if cfg:
+        v.config(**cfg)
+    if edges is not None:
+        v.set_grid(edges)
+    grids, hists = [], []
+    for n, adapt in schedule:
+        grids.append(v.grid())
+        v.iterate(n, adapt)
+        if adapt:
+            hists.append(v.histogram())
+            v.refine(alpha)
+    rows = v.iterations()
+    final = v.grid()
+    res = v.result(first_iter)
+    v.close()
+    return dict(rows=rows, grids=grids, hists=hists, edges=final, result=res)
+
+
+def rel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300))
+
+
+def assert_fp64_parity(g, o, schedule):
+    for t, (n, adapt) in enumerate(schedule):
+        row, ref = g["rows"][t], o["log"][t]
+        assert row[2] == n
+        assert rel(row[4], ref["I"]) < RTOL64, (t, row[4], ref["I"])
+        assert rel(row[5], ref["var"]) < 1e-10, (t, row[5], ref["var"])
+        assert row[3] == ref["nonfinite"]
+        assert np.allclose(g["grids"][t], o["grids"][t], rtol=RTOL64, atol=1e-15)
+    k = 0
+    for t, (n, adapt) in enumerate(schedule):
+        if adapt:
+            assert np.allclose(g["hists"][k], o["log"][t]["hist"], rtol=1e-11, atol=0), t
+            k += 1
+    assert np.allclose(g["edges"], o["edges"], rtol=RTOL64, atol=1e-15)
+
+
+# ---------------------------------------------------------------- RNG
+def test_philox_words_bit_exact():
+    """GPU Philox words == oracle words on counters that cross the 32-bit carry
+    of the sample index, for several dims, iterations and integral ids."""
+    for seed, ident, it, i0, n, dim in [(1, 0, 0, 0, 4096, 8), (0xDEADBEEF12345678, 3, 7,
+                                        2**32 - 1000, 2000, 5), (2**64 - 1, 255, 2**32 - 1, 2**40,
+                                        700, 16), (42, 1, 1, 12345, 1001, 1)]:
+        out = torch.empty((n, dim), dtype=torch.int32, device="cuda")
+        V.vegas_sample_words(seed, ident, it, i0, n, dim, out.data_ptr(),
+                             torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint32)
+        sel = np.unique(np.concatenate([np.arange(0, n, 7), [n - 1]]))
+        ref = np.array([oracle.sample_words(seed, ident, it, i0 + int(r), dim) for r in sel])
+        assert np.array_equal(got[sel], ref)
+
+
+def test_philox_words_bulk_1e6():
+    n, dim = 1 << 18, 4
+    out = torch.empty((n, dim), dtype=torch.int32, device="cuda")
+    V.vegas_sample_words(9, 0, 3, 2**32 - n // 2, n, dim, out.data_ptr(),
+                         torch.cuda.current_stream().cuda_stream)
+    got = out.cpu().numpy().view(np.uint32)
+    i = 2**32 - n // 2 + np.arange(n, dtype=np.uint64)
+    ctrs = np.stack([(i & 0xFFFFFFFF).astype(np.uint32), (i >> 32).astype(np.uint32),
+                     np.zeros(n, np.uint32), np.full(n, 3, np.uint32)], axis=1)
+    ref = oracle.philox(ctrs, np.array([9, 0], dtype=np.uint32))
+    assert np.array_equal(got, ref)
+
+
+# ---------------------------------------------------------------- FP64 parity
+def test_fp64_lepage_gauss_d4_run():
+    """The d=4 Lepage Gaussian, 5 adapting iterations of 1e5 (a=0.1, 50 bins)."""
+    wl = W.c1_gauss4()
+    o = oracle.run(wl.dim, wl.nbins, wl.seed, wl.integrand, wl.params, wl.schedule, nthreads=8)
+    g = gpu_run(wl.dim, wl.nbins, wl.seed, wl.integrand, wl.params, wl.schedule, V.VEGAS_FP64)
+    assert_fp64_parity(g, o, wl.schedule)
+    m, s, c, n, bad = g["result"]
+    assert n == 5 and not bad
+    assert rel(m, o["mean"]) < RTOL64 and rel(s, o["sigma"]) < 1e-10
+
+
+def test_fp64_gauss_d8_adapt_then_fixed():
+    """d=8 Gaussian: adapting then fixed-grid iterations (reduced sizes)."""
+    sched = [(200_000, 1)] * 4 + [(500_001, 0)] * 2
+    p = W.gauss_params(8, 0.1)
+    o = oracle.run(8, 50, 2, W.GAUSS, p, sched, nthreads=8, first_iter=4)
+    g = gpu_run(8, 50, 2, W.GAUSS, p, sched, V.VEGAS_FP64, first_iter=4)
+    assert_fp64_parity(g, o, sched)
+    m, s, c, n, bad = g["result"]
+    assert n == 6 and rel(m, o["mean"]) < RTOL64 and rel(s, o["sigma"]) < 1e-10
+    assert rel(c, o["chi2_dof"]) < 1e-8
+
+
+@pytest.mark.parametrize("fid,dim,nbins", [(W.GAUSS_MIX2, 3, 37), (W.FLAT, 5, 7),
+                                           (W.GENZ_DISC, 4, 20), (W.GENZ_PPEAK, 6, 25),
+                                           (W.GAUSS, 1, 2), (W.GAUSS, 16, 100),
+                                           (W.GAUSS, 2, 1024), (W.GAUSS, 8, 1)])
+def test_fp64_integrands_and_shapes(fid, dim, nbins):
+    if fid in (W.GAUSS, ):
+        p = W.gauss_params(dim, 0.2, np.linspace(0.3, 0.7, dim))
+    elif fid == W.GAUSS_MIX2:
+        p = W.mix2_params(dim, 0.15)
+    elif fid == W.FLAT:
+        p = []
+    else:
+        p = W.genz_params(dim, seed=dim, kind=fid)
+    sched = [(30_011, 1), (20_000, 1), (12_345, 0)]
+    edges = W.random_monotone_grid(dim, nbins, seed=dim + nbins, spread=0.8) if nbins > 1 else None
+    o = oracle.run(dim, nbins, 17, fid, p, sched, edges=edges, nthreads=8)
+    g = gpu_run(dim, nbins, 17, fid, p, sched, V.VEGAS_FP64, edges=edges)
+    assert_fp64_parity(g, o, sched)
+
+
+@pytest.mark.parametrize("n", [2, 3, 31, 33, 255, 257, 1000])
+def test_fp64_tiny_and_ragged_n(n):
+    p = W.gauss_params(3, 0.3, [0.2, 0.5, 0.8])
+    sched = [(n, 1), (n, 0)]
+    o = oracle.run(3, 10, 5, W.GAUSS, p, sched)
+    g = gpu_run(3, 10, 5, W.GAUSS, p, sched, V.VEGAS_FP64)
+    assert_fp64_parity(g, o, sched)
+
+
+def test_launch_configuration_and_chunking_do_not_change_results():
+    """Counters are a function of the sample index only: any block size, grid
+    size or chunking gives the same sums (up to summation order)."""
+    p = W.gauss_params(5, 0.1)
+    sched = [(300_007, 1), (300_007, 1), (123_457, 0)]
+    base = gpu_run(5, 50, 3, W.GAUSS, p, sched, V.VEGAS_FP64)
+    for cfg in [dict(block_threads=64), dict(block_threads=128, blocks_per_sm=1),
+                dict(chunk_samples=77_777), dict(min_samples_per_thread=1000)]:
+        g = gpu_run(5, 50, 3, W.GAUSS, p, sched, V.VEGAS_FP64, cfg=cfg)
+        assert rel(g["rows"][:, 4], base["rows"][:, 4]) < 1e-13
+        assert np.allclose(g["edges"], base["edges"], rtol=1e-13, atol=1e-16)
+
+
+def test_fp64_nonfinite_is_counted_and_reported():
+    """A width of 1e-300 makes the Gaussian's prefactor overflow: every f J is
+    non-finite, is left out of the sums and vegas_result reports it."""
+    p = [1e-300, 0.5, 0.5]
+    o = oracle.iterate(oracle.uniform_grid(2, 10), 1, 0, 1000, W.GAUSS, p, adapt=True)
+    g = gpu_run(2, 10, 1, W.GAUSS, p, [(1000, 1)], V.VEGAS_FP64)
+    assert g["rows"][0][3] == o["nonfinite"] == 1000
+    assert g["rows"][0][0] == 0.0
+    assert g["result"][4] is True
+
+
+# ---------------------------------------------------------------- FP32-eval mode
+@pytest.mark.parametrize("fid,dim,nbins,tol", [(W.GAUSS, 4, 50, 1e-5), (W.GAUSS, 8, 50, 1e-5),
+                                               (W.GAUSS_MIX2, 16, 100, 3e-5),
+                                               (W.GENZ_PPEAK, 6, 30, 1e-5),
+                                               (W.GENZ_DISC, 5, 30, 1e-5), (W.FLAT, 3, 11, 1e-6)])
+def test_fp32_single_iteration_against_fp64_oracle(fid, dim, nbins, tol):
+    """Same grid and counters: the float path's I and var are within the float
+    error budget of the FP64 oracle's."""
+    if fid == W.GAUSS:
+        p = W.gauss_params(dim, 0.1)
+    elif fid == W.GAUSS_MIX2:
+        p = W.mix2_params(dim, 0.1)
+    elif fid == W.FLAT:
+        p = []
+    else:
+        p = W.genz_params(dim, seed=2 * dim, kind=fid)
+    warm = oracle.run(dim, nbins, 99, fid, p, [(100_000, 1)] * 4, nthreads=8)
+    e = warm["edges"]
+    o = oracle.iterate(e, 7, 0, 400_000, fid, p, adapt=True, nthreads=8)
+    g = gpu_run(dim, nbins, 7, fid, p, [(400_000, 1)], V.VEGAS_FP32_EVAL, edges=e)
+    row = g["rows"][0]
+    assert abs(row[4] - o["I"]) <= tol * abs(o["I"]) + 1e-300
+    if o["var"] > 0:
+        assert abs(row[5] - o["var"]) <= 10 * tol * o["var"]
+    h = g["hists"][0]
+    assert np.allclose(h.sum(axis=1), o["hist"].sum(axis=1), rtol=10 * tol)
+
+
+def test_fp32_lepage_gauss_d4_within_3_sigma():
+    wl = W.c1_gauss4()
+    g = gpu_run(wl.dim, wl.nbins, wl.seed, wl.integrand, wl.params, wl.schedule,
+                V.VEGAS_FP32_EVAL)
+    o = oracle.run(wl.dim, wl.nbins, wl.seed, wl.integrand, wl.params, wl.schedule, nthreads=8)
+    m, s, c, n, bad = g["result"]
+    assert abs(m - o["mean"]) < 3 * np.hypot(s, o["sigma"]) / np.sqrt(2) + 1e-12 or \
+        abs(m - o["mean"]) < 1e-4 * abs(o["mean"])
+    assert abs(m - erf(5.0) ** 4) < 4 * s
+
+
+def test_fp32_gauss_d8_close_to_fp64_gpu():
+    """Same counters: the float and double runs differ by far less than their
+    Monte Carlo error, and their errors agree to 1%."""
+    sched = [(1_000_000, 1)] * 6 + [(2_000_000, 0)] * 2
+    p = W.gauss_params(8, 0.1)
+    g32 = gpu_run(8, 50, 2, W.GAUSS, p, sched, V.VEGAS_FP32_EVAL, first_iter=6)
+    g64 = gpu_run(8, 50, 2, W.GAUSS, p, sched, V.VEGAS_FP64, first_iter=6)
+    m32, s32 = g32["result"][:2]
+    m64, s64 = g64["result"][:2]
+    assert abs(m32 - m64) < 0.1 * s64
+    assert abs(s32 / s64 - 1.0) < 0.01
+    assert abs(m64 - erf(5.0) ** 8) < 4 * s64
+    assert np.allclose(g32["edges"], g64["edges"], rtol=0, atol=1e-3)
