@@ -160,7 +160,8 @@ LAUNCHES_PER_STEP = 1 + IT_ADAPT * 2 + IT_FIXED  # init, iterate+refine, fixed i
 
 
 def time_mode(V, mode, steps, warmup, seed0, ws, flush, stream):
-    """Device time of `steps` whole steps (events on the library's stream)."""
+    """Device time of `steps` whole steps (events on the library's stream);
+    step s uses seed seed0 + s, and the result returned is the last step's."""
     import torch
 
     handles = []
@@ -306,8 +307,9 @@ def main():
     value = SAMPLES_PER_STEP * args.steps * world / (total_ms / 1e3)
 
     # plain FP64 on the same counters (equal error)
-    ms64, fixed64, res64 = time_mode(V, V.VEGAS_FP64, args.fp64_steps, 1, seed0, ws, flush,
-                                     stream)
+    # (its last step uses the same seed as the FP32 run's last step)
+    ms64, fixed64, res64 = time_mode(V, V.VEGAS_FP64, args.fp64_steps, 1,
+                                     seed0 + args.steps - args.fp64_steps, ws, flush, stream)
     value64 = SAMPLES_PER_STEP * args.fp64_steps / (sum(ms64) / 1e3)
 
     # end to end through the public API with host buffers

@@ -55,12 +55,23 @@ def rel(a, b):
     return np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300))
 
 
+def fp64_tol(edges):
+    """Relative tolerance of I in FP64 mode on a grid that both sides refined.
+    The two refinements agree to about one ulp of the edges, and a width
+    Delta = e_{j+1} - e_j then carries a relative error of eps/Delta, which the
+    Jacobian prod_k N Delta_k accumulates over the d dimensions: bound
+    8 d eps / min Delta, and never below the 1e-12 target."""
+    dmin = np.min(np.diff(edges, axis=1))
+    return max(RTOL64, 8 * edges.shape[0] * np.finfo(float).eps / dmin)
+
+
 def assert_fp64_parity(g, o, schedule):
     for t, (n, adapt) in enumerate(schedule):
         row, ref = g["rows"][t], o["log"][t]
+        tol = fp64_tol(o["grids"][t]) if t > 0 else RTOL64
         assert row[2] == n
-        assert rel(row[4], ref["I"]) < RTOL64, (t, row[4], ref["I"])
-        assert rel(row[5], ref["var"]) < 1e-10, (t, row[5], ref["var"])
+        assert rel(row[4], ref["I"]) < tol, (t, row[4], ref["I"], tol)
+        assert rel(row[5], ref["var"]) < 100 * tol, (t, row[5], ref["var"], tol)
         assert row[3] == ref["nonfinite"]
         assert np.allclose(g["grids"][t], o["grids"][t], rtol=RTOL64, atol=1e-15)
     k = 0
@@ -200,8 +211,9 @@ def test_fp32_single_iteration_against_fp64_oracle(fid, dim, nbins, tol):
     g = gpu_run(dim, nbins, 7, fid, p, [(400_000, 1)], V.VEGAS_FP32_EVAL, edges=e)
     row = g["rows"][0]
     assert abs(row[4] - o["I"]) <= tol * abs(o["I"]) + 1e-300
-    if o["var"] > 0:
-        assert abs(row[5] - o["var"]) <= 10 * tol * o["var"]
+    # a per-sample relative error delta of f J moves S2/n - I^2 by about
+    # 2 delta (var n + I^2), so var moves by 2 delta (var + I^2/n)
+    assert abs(row[5] - o["var"]) <= 10 * tol * (o["var"] + o["I"] ** 2 / 400_000)
     h = g["hists"][0]
     assert np.allclose(h.sum(axis=1), o["hist"].sum(axis=1), rtol=10 * tol)
 
