@@ -169,6 +169,43 @@ int vegas_get_histogram(vegas_state *s, double *host_hist);
 int vegas_sample_words(uint64_t seed, uint32_t integral_id, uint32_t iter, uint64_t i0,
                        uint64_t n, int dim, uint32_t *d_out, void *cuda_stream);
 
+/* ---- entry point for callers that cannot allocate device memory ---------- */
+/* The paper has no counterpart to this call; it exists for callers that are not
+ * allowed to allocate device memory -- code that runs inside a host framework
+ * which owns every device allocation (a plug-in in someone else's process, an
+ * embedded runtime with a fixed memory budget), or code that only holds the
+ * buffers it was handed.  Such callers cannot provide the workspace the
+ * vegas_init_grid path needs.
+ *
+ * vegas_iterate_noalloc runs one iteration of the VEGAS_GAUSS integrand
+ * (params = [a, mu_1 .. mu_d]) on the grid d_edges (dim x (nbins+1) device
+ * doubles) with the counters of iteration `iter`, writes
+ * {S1, S2, n, nonfinite, I, var} to d_result (6 device doubles) and, when
+ * adapt != 0, refines d_edges in place with damping alpha (the same kernels and
+ * rules as vegas_iterate + vegas_refine).  It allocates nothing: its scratch
+ * (block partials, a ticket word, the histogram) is one static device array of
+ * VEGAS_NOALLOC_SCRATCH_BYTES bytes in the library, which every GPU that loads
+ * the library holds until the process exits.
+ *   - dim * nbins > VEGAS_NOALLOC_MAX_DIM_X_BINS returns VEGAS_ENOSPACE (the
+ *     histogram would not fit the scratch); the launch never uses more than
+ *     VEGAS_NOALLOC_MAX_BLOCKS blocks.
+ *   - The first call on a device looks up the scratch's device address on that
+ *     device (cudaGetSymbolAddress); make that first call before any stream
+ *     capture starts.
+ *   - Every call shares the one scratch array and it keeps the last call's
+ *     contents; each call clears what must start at zero.  Calls whose work
+ *     overlaps on the GPU (other streams, other host threads) race on the
+ *     scratch: order them on one stream.
+ *   - In FP32 mode the sums are not pre-scaled by a previous estimate (there is
+ *     none); the built-in integrand is normalised, so none is needed.
+ * Asynchronous on the stream; n_samples in [2, 2^40]. */
+#define VEGAS_NOALLOC_MAX_DIM_X_BINS 4096
+#define VEGAS_NOALLOC_MAX_BLOCKS 2048
+#define VEGAS_NOALLOC_SCRATCH_BYTES 98560
+int vegas_iterate_noalloc(double *d_edges, int dim, int nbins, uint64_t seed, uint32_t iter,
+                          int mode, const double *params, int nparams, uint64_t n_samples,
+                          int adapt, double alpha, double *d_result, void *cuda_stream);
+
 /* Release the descriptor (not the caller's workspace).  Synchronises the
  * stream first.  NULL is accepted. */
 int vegas_destroy(vegas_state *s);

@@ -16,13 +16,14 @@ VEGAS_OK, VEGAS_EINVAL, VEGAS_ECUDA, VEGAS_ENONFINITE, VEGAS_ESTATE, VEGAS_ENOSP
 VEGAS_FP64, VEGAS_FP32_EVAL = 0, 1
 VEGAS_GAUSS, VEGAS_GAUSS_MIX2, VEGAS_FLAT, VEGAS_GENZ_DISC, VEGAS_GENZ_PPEAK = range(5)
 VEGAS_MAX_DIM, VEGAS_MAX_BINS, VEGAS_MAX_DIM_X_BINS = 16, 1024, 8192
+VEGAS_NOALLOC_MAX_DIM_X_BINS, VEGAS_NOALLOC_MAX_BLOCKS = 4096, 2048
 LOG_COLUMNS = ("S1", "S2", "n", "nonfinite", "I", "var")
 
 # every symbol include/vegas.h declares
 EXPORTED = ("vegas_workspace_bytes", "vegas_init_grid", "vegas_set_config", "vegas_iterate",
             "vegas_refine", "vegas_result", "vegas_get_iterations", "vegas_get_grid",
             "vegas_set_grid", "vegas_get_histogram", "vegas_sample_words", "vegas_destroy",
-            "vegas_strerror")
+            "vegas_strerror", "vegas_iterate_noalloc")
 
 
 class VegasError(RuntimeError):
@@ -64,6 +65,8 @@ def lib():
         L.vegas_get_histogram.argtypes = [vp, vp]
         L.vegas_sample_words.argtypes = [u64, ctypes.c_uint32, ctypes.c_uint32, u64, u64, i32, vp,
                                          vp]
+        L.vegas_iterate_noalloc.argtypes = [vp, i32, i32, u64, ctypes.c_uint32, i32, vp, i32, u64,
+                                             i32, dbl, vp, vp]
         L.vegas_destroy.argtypes = [vp]
         L.vegas_strerror.argtypes = [i32]
         L.vegas_strerror.restype = ctypes.c_char_p
@@ -155,6 +158,18 @@ def vegas_sample_words(seed, integral_id, it, i0, n, dim, d_out, cuda_stream):
     """Philox words of samples i0 .. i0+n-1 into the device buffer d_out (n x dim uint32)."""
     _check(lib().vegas_sample_words(seed & (2**64 - 1), integral_id, it, i0, n, dim, d_out,
                                     cuda_stream), "vegas_sample_words")
+
+
+def vegas_iterate_noalloc(d_edges, dim, nbins, seed, it, mode, params, n_samples, adapt, alpha,
+                          d_result, cuda_stream):
+    """One Gaussian iteration without any device allocation (see include/vegas.h):
+    d_edges (dim x (nbins+1) doubles) and d_result (6 doubles) are device
+    addresses owned by the caller."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    _check(lib().vegas_iterate_noalloc(d_edges, dim, nbins, seed & (2**64 - 1), it, mode,
+                                       p.ctypes.data, int(p.size), int(n_samples),
+                                       1 if adapt else 0, float(alpha), d_result, cuda_stream),
+           "vegas_iterate_noalloc")
 
 
 def vegas_destroy(h):

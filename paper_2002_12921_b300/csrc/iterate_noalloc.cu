@@ -1,0 +1,300 @@
+// vegas_iterate_noalloc: one Vegas iteration (plus the refinement when adapting)
+// for callers that may not allocate device memory.
+//
+// Everything the iteration needs besides the caller's inputs and outputs -- the
+// per-block partial sums, the last-block ticket and the (fJ)^2 histogram -- lives
+// in one file-scope device array.  Host code may not use that array's name as a
+// pointer (on the host it names a host-side stand-in, not device memory), so
+// each device's address of it is looked up once with cudaGetSymbolAddress, with
+// that device current, and passed to the kernels.
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "iterate_kernel.cuh"
+
+namespace vegas {
+namespace {
+
+constexpr int kNaMaxBlocks = VEGAS_NOALLOC_MAX_BLOCKS;
+constexpr int kNaMaxDimBins = VEGAS_NOALLOC_MAX_DIM_X_BINS;
+// scratch layout: partials | histogram | control words
+constexpr size_t kNaPartials = 0;
+constexpr size_t kNaHist = kNaPartials + (size_t)kNaMaxBlocks * kPartialStride * sizeof(double);
+constexpr size_t kNaCtrl = kNaHist + (size_t)kNaMaxDimBins * sizeof(double);
+constexpr size_t kNaBytes = kNaCtrl + kCtrlWords * sizeof(unsigned);
+static_assert(kNaBytes == VEGAS_NOALLOC_SCRATCH_BYTES, "scratch size in vegas.h");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+constexpr int kNaMaxDevices = 64;
+std::mutex g_setup_mutex;
+unsigned char* g_scratch_ptr[kNaMaxDevices] = {};
+
+// The device address of the scratch on `device` (current), looked up once.
+cudaError_t scratch_address(int device, unsigned char** out) {
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_ptr[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[device] = static_cast<unsigned char*>(p);
+    }
+    *out = g_scratch_ptr[device];
+    return cudaSuccess;
+}
+
+struct NoAllocArgs {
+    const double* edges;
+    double* hist;       // scratch
+    double* partials;   // scratch
+    unsigned* ticket;   // scratch
+    double* out;        // caller: S1, S2, n, nonfinite, I, var
+    unsigned long long n;
+    unsigned iter;
+    int nbins;
+    unsigned rk0[10], rk1[10];
+    FnConsts fc;
+};
+
+// The iterate kernel with its scratch taken from the arguments above and its
+// result written to the caller's six doubles (one launch per iteration, no
+// pre-scale from a previous estimate).
+template <typename R, int D, int FN, bool ADAPT>
+__global__ void __launch_bounds__(256) noalloc_iterate_kernel(const NoAllocArgs a) {
+    using P = Prec<R>;
+    using Pair = typename P::Pair;
+    using H = typename P::Hist;
+    constexpr int DC = (D + 3) / 4;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double sred[32];
+    __shared__ unsigned sbad[32];
+    __shared__ int s_last;
+
+    const int N = a.nbins;
+    Pair* sgrid = reinterpret_cast<Pair*>(smem_raw);
+    H* shist = reinterpret_cast<H*>(sgrid + D * N);
+    for (int idx = threadIdx.x; idx < D * N; idx += blockDim.x) {
+        const int k = idx / N, j = idx - k * N;
+        const double* e = a.edges + (size_t)k * (N + 1) + j;
+        sgrid[idx] = P::pair(e[0], e[1]);
+        if (ADAPT) shist[idx] = H(0);
+    }
+    const R jstart = (R)(sizeof(R) == 4 ? a.fc.C32 : a.fc.C);
+    const R n4 = (R)((double)N * N * N * N);
+    double nrem = 1.0;
+    for (int r = 0; r < D % 4; ++r) nrem *= N;
+    const R nlast = (R)nrem;
+    __syncthreads();
+
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    Acc<R> acc;
+    unsigned bad = 0;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+         i += stride) {
+        Integrand<R, FN> f;
+        f.begin();
+        R J = jstart;
+        int hb[D];
+#pragma unroll
+        for (int q = 0; q < DC; ++q) {
+            uint32_t w0 = (uint32_t)i, w1 = (uint32_t)(i >> 32), w2 = (uint32_t)q, w3 = a.iter;
+            philox4x32_10(w0, w1, w2, w3, a.rk0, a.rk1);
+            const uint32_t w[4] = {w0, w1, w2, w3};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int k = 4 * q + t;
+                if (k < D) {
+                    const uint32_t j = __umulhi(w[t], (uint32_t)N);
+                    const uint32_t l = w[t] * (uint32_t)N;
+                    const Pair g = sgrid[k * N + j];
+                    const R x = P::fma(P::frac(l), g.y, g.x);
+                    J *= g.y;
+                    f.add(k, x, a.fc);
+                    if (ADAPT) hb[k] = k * N + (int)j;
+                }
+            }
+            if (sizeof(R) == 4) J *= (4 * q + 4 <= D) ? n4 : nlast;
+        }
+        const R fw = f.value(a.fc) * J;
+        if (P::finite(fw)) {
+            acc.add(fw);
+            if (ADAPT) {
+                const R fw2 = fw * fw;
+#pragma unroll
+                for (int k = 0; k < D; ++k) atomicAdd(&shist[hb[k]], (H)fw2);
+            }
+        } else {
+            ++bad;
+        }
+    }
+
+    const double b1 = block_sum(acc.sum1(), sred);
+    const double b2 = block_sum(acc.sum2(), sred);
+    const unsigned bb = block_sum(bad, sbad);
+    if (ADAPT) {
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < D * N; idx += blockDim.x) {
+            const H v = shist[idx];
+            if (v != H(0)) atomicAdd(&a.hist[idx], (double)v);
+        }
+    }
+    if (threadIdx.x == 0) {
+        double* p = a.partials + (size_t)blockIdx.x * kPartialStride;
+        p[0] = b1;
+        p[1] = b2;
+        p[2] = (double)bb;
+        __threadfence();
+        const unsigned ticket = atomicAdd(a.ticket, 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double t1 = 0.0, t2 = 0.0, tb = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        const double* p = a.partials + (size_t)b * kPartialStride;
+        t1 += __ldcg(p + 0);
+        t2 += __ldcg(p + 1);
+        tb += __ldcg(p + 2);
+    }
+    t1 = block_sum(t1, sred);
+    t2 = block_sum(t2, sred);
+    tb = block_sum(tb, sred);
+    if (threadIdx.x == 0) {
+        const double n = (double)a.n;
+        const double I = t1 / n;
+        const double var = (t2 / n - I * I) / (n - 1.0);
+        a.out[0] = t1;
+        a.out[1] = t2;
+        a.out[2] = n;
+        a.out[3] = tb;
+        a.out[4] = I;
+        a.out[5] = var > 0.0 ? var : 0.0;
+        *a.ticket = 0u;
+    }
+}
+
+#define NA_ROW(R, D) \
+    {(const void*)&noalloc_iterate_kernel<R, D, VEGAS_GAUSS, false>, \
+     (const void*)&noalloc_iterate_kernel<R, D, VEGAS_GAUSS, true>}
+
+const void* noalloc_kernel(int mode, int dim, bool adapt) {
+    static const void* const f32[kMaxDim][2] = {
+        NA_ROW(float, 1),  NA_ROW(float, 2),  NA_ROW(float, 3),  NA_ROW(float, 4),
+        NA_ROW(float, 5),  NA_ROW(float, 6),  NA_ROW(float, 7),  NA_ROW(float, 8),
+        NA_ROW(float, 9),  NA_ROW(float, 10), NA_ROW(float, 11), NA_ROW(float, 12),
+        NA_ROW(float, 13), NA_ROW(float, 14), NA_ROW(float, 15), NA_ROW(float, 16)};
+    static const void* const f64[kMaxDim][2] = {
+        NA_ROW(double, 1),  NA_ROW(double, 2),  NA_ROW(double, 3),  NA_ROW(double, 4),
+        NA_ROW(double, 5),  NA_ROW(double, 6),  NA_ROW(double, 7),  NA_ROW(double, 8),
+        NA_ROW(double, 9),  NA_ROW(double, 10), NA_ROW(double, 11), NA_ROW(double, 12),
+        NA_ROW(double, 13), NA_ROW(double, 14), NA_ROW(double, 15), NA_ROW(double, 16)};
+    return (mode == VEGAS_FP32_EVAL ? f32 : f64)[dim - 1][adapt ? 1 : 0];
+}
+
+struct Guard {
+    int prev = -1;
+    bool ok = true;
+    explicit Guard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~Guard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+}  // namespace vegas
+
+extern "C" int vegas_iterate_noalloc(double* d_edges, int dim, int nbins, uint64_t seed,
+                                     uint32_t iter, int mode, const double* params, int nparams,
+                                     uint64_t n_samples, int adapt, double alpha,
+                                     double* d_result, void* cuda_stream) {
+    using namespace vegas;
+    if (dim < 1 || dim > kMaxDim || nbins < 1 || nbins > kMaxBins) return VEGAS_EINVAL;
+    if (dim * nbins > kNaMaxDimBins) return VEGAS_ENOSPACE;
+    if (mode != VEGAS_FP64 && mode != VEGAS_FP32_EVAL) return VEGAS_EINVAL;
+    if (!d_edges || !d_result || !params || nparams < 1 + dim) return VEGAS_EINVAL;
+    if (n_samples < 2 || n_samples > (1ull << 40)) return VEGAS_EINVAL;
+    if (adapt && !(alpha >= 0.0 && std::isfinite(alpha))) return VEGAS_EINVAL;
+    for (int i = 0; i < 1 + dim; ++i)
+        if (!std::isfinite(params[i])) return VEGAS_EINVAL;
+    const double a_width = params[0];
+    if (!(a_width > 0.0)) return VEGAS_EINVAL;
+
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, d_edges) != cudaSuccess ||
+        attr.type != cudaMemoryTypeDevice || attr.device < 0 || attr.device >= kNaMaxDevices) {
+        cudaGetLastError();
+        return VEGAS_EINVAL;
+    }
+    Guard g(attr.device);
+    if (!g.ok) return VEGAS_ECUDA;
+    unsigned char* scratch = nullptr;
+    if (scratch_address(attr.device, &scratch) != cudaSuccess) return VEGAS_ECUDA;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+
+    // Gaussian constants (Eq. 1): (a sqrt(pi))^-d, with N^d for the FP64 Jacobian
+    NoAllocArgs a;
+    std::memset(&a, 0, sizeof(a));
+    const double norm = std::pow(a_width * std::sqrt(M_PI), -(double)dim);
+    const double kappa = std::sqrt(1.4426950408889634) / a_width;
+    a.fc.C = norm * std::pow((double)nbins, dim);
+    a.fc.C32 = norm;
+    a.fc.inv_a2 = 1.0 / (a_width * a_width);
+    a.fc.kappa = (float)kappa;
+    for (int k = 0; k < dim; ++k) {
+        a.fc.p0[k] = params[1 + k];
+        a.fc.q0[k] = (float)(-params[1 + k] * kappa);
+    }
+    philox_round_keys(seed, a.rk0, a.rk1);
+    a.edges = d_edges;
+    a.hist = reinterpret_cast<double*>(scratch + kNaHist);
+    a.partials = reinterpret_cast<double*>(scratch + kNaPartials);
+    a.ticket = reinterpret_cast<unsigned*>(scratch + kNaCtrl);
+    a.out = d_result;
+    a.n = n_samples;
+    a.iter = iter;
+    a.nbins = nbins;
+
+    // what must start at zero: the ticket and, when adapting, the histogram
+    if (cudaMemsetAsync(scratch + kNaCtrl, 0, kCtrlWords * sizeof(unsigned), stream) != cudaSuccess)
+        return VEGAS_ECUDA;
+    if (adapt && cudaMemsetAsync(scratch + kNaHist, 0, (size_t)dim * nbins * sizeof(double),
+                                 stream) != cudaSuccess)
+        return VEGAS_ECUDA;
+
+    const bool ad = adapt != 0;
+    const void* kern = noalloc_kernel(mode, dim, ad);
+    const size_t smem = iterate_smem_bytes(mode, dim, nbins, ad);
+    if (smem > 40 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+        return VEGAS_ECUDA;
+    int occ = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem) != cudaSuccess ||
+        occ < 1 ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, attr.device) != cudaSuccess)
+        return VEGAS_ECUDA;
+    long long grid = (long long)((n_samples + 256 * 8 - 1) / (256 * 8));
+    if (grid > (long long)sms * occ) grid = (long long)sms * occ;
+    if (grid > kNaMaxBlocks) grid = kNaMaxBlocks;
+    void* args[] = {&a};
+    if (cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(256), args, smem, stream) != cudaSuccess)
+        return VEGAS_ECUDA;
+    if (ad) {
+        RefineArgs r;
+        r.edges = d_edges;
+        r.hist = a.hist;
+        r.dim = dim;
+        r.nbins = nbins;
+        r.alpha = alpha;
+        if (launch_refine(r, stream) != cudaSuccess) return VEGAS_ECUDA;
+    }
+    return VEGAS_OK;
+}
