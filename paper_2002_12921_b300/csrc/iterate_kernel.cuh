@@ -28,6 +28,13 @@
 
 namespace vegas {
 
+// 2^x with the hardware exponential (flush-to-zero for tiny results).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ------------------------------------------------------------------------
 // Integrands.  begin() resets the running state, add(k, x) folds in
 // dimension k (a compile-time constant once the kernel's loops are unrolled,
@@ -46,7 +53,7 @@ struct Integrand<float, VEGAS_GAUSS> {
         const float u = fmaf(x, c.kappa, c.q0[k]);
         s = fmaf(u, u, s);
     }
-    __device__ __forceinline__ float value(const FnConsts&) const { return exp2f(-s); }
+    __device__ __forceinline__ float value(const FnConsts&) const { return ex2_approx(-s); }
 };
 
 template <>
@@ -60,7 +67,7 @@ struct Integrand<float, VEGAS_GAUSS_MIX2> {
         sb = fmaf(ub, ub, sb);
     }
     __device__ __forceinline__ float value(const FnConsts&) const {
-        return exp2f(-sa) + exp2f(-sb);
+        return ex2_approx(-sa) + ex2_approx(-sb);
     }
 };
 
@@ -82,7 +89,7 @@ struct Integrand<float, VEGAS_GENZ_DISC> {
         inside = inside && (x > c.q0[k]);
     }
     __device__ __forceinline__ float value(const FnConsts&) const {
-        return inside ? exp2f(s) : 0.f;
+        return inside ? ex2_approx(s) : 0.f;
     }
 };
 
@@ -161,23 +168,29 @@ struct Integrand<double, VEGAS_GENZ_PPEAK> {
 };
 
 // ------------------------------------------------------------------------
-// Precision-specific pieces of the map.
+// Precision-specific pieces of the map.  unit(l) is the number in [1, 2) whose
+// mantissa holds the position bits; the staged pair is (e - (1 - u/2) Delta,
+// Delta) with u the unit's spacing, so that x = fma(unit, Delta, e') is
+// e + frac Delta with frac = unit - (1 - u/2) in (0, 1): for float,
+// frac = (floor(l / 2^9) + 1/2) 2^-23; for double, frac = (l + 1/2) 2^-32.
+// Folding the offset into the staged edge saves one add per dimension; it moves
+// x by at most an ulp of the edge.
 // ------------------------------------------------------------------------
 template <typename R>
 struct Prec;
 
 template <>
 struct Prec<float> {
-    using Pair = float2;  // (edge, width) of one bin, in shared memory
+    using Pair = float2;  // (shifted edge, width) of one bin, in shared memory
     using Hist = float;
-    // frac = (floor(l / 2^9) + 1/2) 2^-23: the float in [1, 2) with those 23
-    // mantissa bits, minus (1 - 2^-24); both steps are exact.
-    static __device__ __forceinline__ float frac(uint32_t l) {
-        return __uint_as_float(0x3F800000u | (l >> 9)) - 0x1.fffffep-1f;
+    static __device__ __forceinline__ float unit(uint32_t l) {
+        // (0x7F : l) >> 9 = 0x3F800000 | (l >> 9): one funnel shift
+        return __uint_as_float(__funnelshift_r(l, 0x7Fu, 9));
     }
     static __device__ __forceinline__ Pair pair(double e0, double e1) {
         const float f0 = (float)e0, f1 = (float)e1;
-        return make_float2(f0, f1 - f0);
+        const float w = f1 - f0;
+        return make_float2(fmaf(-0x1.fffffep-1f, w, f0), w);
     }
     static __device__ __forceinline__ bool finite(float v) { return fabsf(v) <= FLT_MAX; }
     static __device__ __forceinline__ float fma(float x, float y, float z) { return fmaf(x, y, z); }
@@ -187,13 +200,13 @@ template <>
 struct Prec<double> {
     using Pair = double2;
     using Hist = double;
-    // frac = (l + 1/2) 2^-32: the double 1 + l 2^-32, minus (1 - 2^-33); exact.
-    static __device__ __forceinline__ double frac(uint32_t l) {
-        return __hiloint2double((int)(0x3FF00000u | (l >> 12)), (int)(l << 20)) -
-               0x1.ffffffffp-1;
+    static __device__ __forceinline__ double unit(uint32_t l) {
+        // high word (0x3FF : l) >> 12 = 0x3FF00000 | (l >> 12), low word l << 20
+        return __hiloint2double((int)__funnelshift_r(l, 0x3FFu, 12), (int)(l << 20));
     }
     static __device__ __forceinline__ Pair pair(double e0, double e1) {
-        return make_double2(e0, e1 - e0);
+        const double w = e1 - e0;
+        return make_double2(::fma(-0x1.ffffffffp-1, w, e0), w);
     }
     static __device__ __forceinline__ bool finite(double v) { return fabs(v) <= DBL_MAX; }
     static __device__ __forceinline__ double fma(double x, double y, double z) {
@@ -256,6 +269,108 @@ struct Acc<double> {
 };
 
 // ------------------------------------------------------------------------
+// Pieces shared by the iterate kernels.
+//
+// Shared memory of a block: the grid as D*N (shifted edge, width) pairs, then,
+// when adapting, the histogram in 2^logr copies laid out [bin][copy]; lane L
+// adds into copy L mod 2^logr, so lanes of one warp never update the same word
+// (with 32 copies every lane also owns its bank).  Shared-memory float and
+// double atomicAdd run as compare-and-swap loops, which then succeed at the
+// first try.
+// ------------------------------------------------------------------------
+template <typename R, int D, bool ADAPT>
+__device__ __forceinline__ void stage_grid(const double* __restrict__ edges, int N, int logr,
+                                           typename Prec<R>::Pair* sgrid,
+                                           typename Prec<R>::Hist* shist) {
+    using P = Prec<R>;
+    for (int idx = threadIdx.x; idx < D * N; idx += blockDim.x) {
+        const int k = idx / N, j = idx - k * N;
+        const double* e = edges + (size_t)k * (N + 1) + j;
+        sgrid[idx] = P::pair(e[0], e[1]);
+    }
+    if (ADAPT)
+        for (int idx = threadIdx.x; idx < (D * N) << logr; idx += blockDim.x)
+            shist[idx] = typename P::Hist(0);
+}
+
+// The samples [first, end) with step `stride` of iteration `it`: Philox words,
+// grid map, integrand, per-thread sums and the shared histogram.
+template <typename R, int D, int FN, bool ADAPT>
+__device__ __forceinline__ void sample_loop(unsigned long long first, unsigned long long end,
+                                            unsigned long long stride, unsigned it,
+                                            uint32_t c2base, const unsigned (&rk0)[10],
+                                            const unsigned (&rk1)[10], const FnConsts& fc,
+                                            int N, int logr, R jstart, R n4, R nlast,
+                                            const typename Prec<R>::Pair* sgrid,
+                                            typename Prec<R>::Hist* shist, Acc<R>& acc,
+                                            unsigned& bad) {
+    using P = Prec<R>;
+    using Pair = typename P::Pair;
+    using H = typename P::Hist;
+    constexpr int DC = (D + 3) / 4;  // Philox calls per sample
+    const int lane_copy = threadIdx.x & ((1 << logr) - 1);
+    for (unsigned long long i = first; i < end; i += stride) {
+        Integrand<R, FN> f;
+        f.begin();
+        R J = jstart;
+        int hb[D];
+#pragma unroll
+        for (int q = 0; q < DC; ++q) {
+            uint32_t w0 = (uint32_t)i, w1 = (uint32_t)(i >> 32), w2 = c2base | (uint32_t)q, w3 = it;
+            philox4x32_10(w0, w1, w2, w3, rk0, rk1);
+            const uint32_t w[4] = {w0, w1, w2, w3};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int k = 4 * q + t;
+                if (k < D) {
+                    const uint32_t j = __umulhi(w[t], (uint32_t)N);
+                    const uint32_t l = w[t] * (uint32_t)N;
+                    const Pair g = sgrid[k * N + j];
+                    const R x = P::fma(P::unit(l), g.y, g.x);
+                    J *= g.y;
+                    f.add(k, x, fc);
+                    if (ADAPT) hb[k] = ((k * N + (int)j) << logr) | lane_copy;
+                }
+            }
+            if (sizeof(R) == 4) J *= (4 * q + 4 <= D) ? n4 : nlast;
+        }
+        const R fw = f.value(fc) * J;
+        if (P::finite(fw)) {
+            acc.add(fw);
+            if (ADAPT) {
+                const R fw2 = fw * fw;
+#pragma unroll
+                for (int k = 0; k < D; ++k) atomicAdd(&shist[hb[k]], (H)fw2);
+            }
+        } else {
+            ++bad;
+        }
+    }
+}
+
+// Add the block's histogram (its copies summed in double, times scale) into the
+// global one: one atomic per non-empty bin.
+template <typename H>
+__device__ __forceinline__ void flush_hist(const H* shist, int nbins_total, int logr,
+                                           double scale, double* hist) {
+    const int R = 1 << logr;
+    for (int idx = threadIdx.x; idx < nbins_total; idx += blockDim.x) {
+        double v = 0.0;
+        for (int c = 0; c < R; ++c) v += (double)shist[(idx << logr) + c];
+        if (v != 0.0) atomicAdd(&hist[idx], v * scale);
+    }
+}
+
+// Jacobian start value and the float path's N^4 / N^(D mod 4) factors.
+template <typename R, int D>
+__device__ __forceinline__ void jacobian_factors(int N, R& n4, R& nlast) {
+    n4 = (R)((double)N * N * N * N);
+    double nrem = 1.0;
+    for (int r = 0; r < D % 4; ++r) nrem *= N;
+    nlast = (R)nrem;
+}
+
+// ------------------------------------------------------------------------
 // The kernel.  R = float or double, D = dimension, FN = integrand id, ADAPT =
 // accumulate the refinement histogram.
 // ------------------------------------------------------------------------
@@ -264,7 +379,6 @@ __global__ void __launch_bounds__(256) vegas_iterate_kernel(const IterArgs a) {
     using P = Prec<R>;
     using Pair = typename P::Pair;
     using H = typename P::Hist;
-    constexpr int DC = (D + 3) / 4;  // Philox calls per sample
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sred[32];
@@ -272,6 +386,7 @@ __global__ void __launch_bounds__(256) vegas_iterate_kernel(const IterArgs a) {
     __shared__ int s_last;
 
     const int N = a.nbins;
+    const int logr = ADAPT ? a.hist_log2r : 0;
     Pair* sgrid = reinterpret_cast<Pair*>(smem_raw);
     H* shist = reinterpret_cast<H*>(sgrid + D * N);
 
@@ -280,14 +395,7 @@ __global__ void __launch_bounds__(256) vegas_iterate_kernel(const IterArgs a) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctrl[kStatus], kStatusLogFull);
         return;
     }
-
-    // Stage the grid as (edge, width) pairs; clear the block's histogram.
-    for (int idx = threadIdx.x; idx < D * N; idx += blockDim.x) {
-        const int k = idx / N, j = idx - k * N;
-        const double* e = a.edges + (size_t)k * (N + 1) + j;
-        sgrid[idx] = P::pair(e[0], e[1]);
-        if (ADAPT) shist[idx] = H(0);
-    }
+    stage_grid<R, D, ADAPT>(a.edges, N, logr, sgrid, shist);
 
     // Pre-scale of the float path: f J is carried as f J 2^-h with 2^h near the
     // previous iteration's estimate; the prefactor enters the Jacobian's start.
@@ -302,73 +410,25 @@ __global__ void __launch_bounds__(256) vegas_iterate_kernel(const IterArgs a) {
     } else {
         j0 = a.fc.C;
     }
-    const R jstart = (R)j0;
-    // float: the factor N^D enters once per Philox group of four dimensions
-    const R n4 = (R)((double)N * N * N * N);
-    double nrem = 1.0;
-    for (int r = 0; r < D % 4; ++r) nrem *= N;
-    const R nlast = (R)nrem;
+    R n4, nlast;
+    jacobian_factors<R, D>(N, n4, nlast);
     __syncthreads();
-
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    const unsigned long long end = a.i0 + a.n_chunk;
-    const uint32_t c2base = a.integral_id << 8;
 
     Acc<R> acc;
     unsigned bad = 0;
-
-    for (unsigned long long i = a.i0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-         i < end; i += stride) {
-        Integrand<R, FN> f;
-        f.begin();
-        R J = jstart;
-        int hb[D];
-#pragma unroll
-        for (int q = 0; q < DC; ++q) {
-            uint32_t w0 = (uint32_t)i, w1 = (uint32_t)(i >> 32), w2 = c2base | (uint32_t)q, w3 = it;
-            philox4x32_10(w0, w1, w2, w3, a.rk0, a.rk1);
-            const uint32_t w[4] = {w0, w1, w2, w3};
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int k = 4 * q + t;
-                if (k < D) {
-                    const uint32_t j = __umulhi(w[t], (uint32_t)N);
-                    const uint32_t l = w[t] * (uint32_t)N;
-                    const Pair g = sgrid[k * N + j];
-                    const R x = P::fma(P::frac(l), g.y, g.x);
-                    J *= g.y;
-                    f.add(k, x, a.fc);
-                    if (ADAPT) hb[k] = k * N + (int)j;
-                }
-            }
-            if (sizeof(R) == 4) J *= (4 * q + 4 <= D) ? n4 : nlast;
-        }
-        const R fw = f.value(a.fc) * J;
-        if (P::finite(fw)) {
-            acc.add(fw);
-            if (ADAPT) {
-                const R fw2 = fw * fw;
-#pragma unroll
-                for (int k = 0; k < D; ++k) atomicAdd(&shist[hb[k]], (H)fw2);
-            }
-        } else {
-            ++bad;
-        }
-    }
+    sample_loop<R, D, FN, ADAPT>(
+        a.i0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x, a.i0 + a.n_chunk,
+        (unsigned long long)gridDim.x * blockDim.x, it, a.integral_id << 8, a.rk0, a.rk1, a.fc,
+        N, logr, (R)j0, n4, nlast, sgrid, shist, acc, bad);
 
     // Block reduction of the sums (fixed order), scaled back by 2^h / 2^2h.
     const double sc1 = ldexp(1.0, h), sc2 = ldexp(1.0, 2 * h);
     const double b1 = block_sum(acc.sum1(), sred);
     const double b2 = block_sum(acc.sum2(), sred);
     const unsigned bb = block_sum(bad, sbad);
-
-    // Flush the block's histogram: one global atomic per non-empty bin.
     if (ADAPT) {
         __syncthreads();
-        for (int idx = threadIdx.x; idx < D * N; idx += blockDim.x) {
-            const H v = shist[idx];
-            if (v != H(0)) atomicAdd(&a.hist[idx], (double)v * sc2);
-        }
+        flush_hist(shist, D * N, logr, sc2, a.hist);
     }
 
     // Publish the block partial; the last block to finish reduces them all in

@@ -54,6 +54,7 @@ struct NoAllocArgs {
     unsigned long long n;
     unsigned iter;
     int nbins;
+    int log2r;          // shared histogram copies (as in the iterate kernel)
     unsigned rk0[10], rk1[10];
     FnConsts fc;
 };
@@ -66,7 +67,6 @@ __global__ void __launch_bounds__(256) noalloc_iterate_kernel(const NoAllocArgs 
     using P = Prec<R>;
     using Pair = typename P::Pair;
     using H = typename P::Hist;
-    constexpr int DC = (D + 3) / 4;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sred[32];
@@ -74,72 +74,28 @@ __global__ void __launch_bounds__(256) noalloc_iterate_kernel(const NoAllocArgs 
     __shared__ int s_last;
 
     const int N = a.nbins;
+    const int logr = ADAPT ? a.log2r : 0;
     Pair* sgrid = reinterpret_cast<Pair*>(smem_raw);
     H* shist = reinterpret_cast<H*>(sgrid + D * N);
-    for (int idx = threadIdx.x; idx < D * N; idx += blockDim.x) {
-        const int k = idx / N, j = idx - k * N;
-        const double* e = a.edges + (size_t)k * (N + 1) + j;
-        sgrid[idx] = P::pair(e[0], e[1]);
-        if (ADAPT) shist[idx] = H(0);
-    }
-    const R jstart = (R)(sizeof(R) == 4 ? a.fc.C32 : a.fc.C);
-    const R n4 = (R)((double)N * N * N * N);
-    double nrem = 1.0;
-    for (int r = 0; r < D % 4; ++r) nrem *= N;
-    const R nlast = (R)nrem;
+    stage_grid<R, D, ADAPT>(a.edges, N, logr, sgrid, shist);
+    R n4, nlast;
+    jacobian_factors<R, D>(N, n4, nlast);
     __syncthreads();
 
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     Acc<R> acc;
     unsigned bad = 0;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
-         i += stride) {
-        Integrand<R, FN> f;
-        f.begin();
-        R J = jstart;
-        int hb[D];
-#pragma unroll
-        for (int q = 0; q < DC; ++q) {
-            uint32_t w0 = (uint32_t)i, w1 = (uint32_t)(i >> 32), w2 = (uint32_t)q, w3 = a.iter;
-            philox4x32_10(w0, w1, w2, w3, a.rk0, a.rk1);
-            const uint32_t w[4] = {w0, w1, w2, w3};
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int k = 4 * q + t;
-                if (k < D) {
-                    const uint32_t j = __umulhi(w[t], (uint32_t)N);
-                    const uint32_t l = w[t] * (uint32_t)N;
-                    const Pair g = sgrid[k * N + j];
-                    const R x = P::fma(P::frac(l), g.y, g.x);
-                    J *= g.y;
-                    f.add(k, x, a.fc);
-                    if (ADAPT) hb[k] = k * N + (int)j;
-                }
-            }
-            if (sizeof(R) == 4) J *= (4 * q + 4 <= D) ? n4 : nlast;
-        }
-        const R fw = f.value(a.fc) * J;
-        if (P::finite(fw)) {
-            acc.add(fw);
-            if (ADAPT) {
-                const R fw2 = fw * fw;
-#pragma unroll
-                for (int k = 0; k < D; ++k) atomicAdd(&shist[hb[k]], (H)fw2);
-            }
-        } else {
-            ++bad;
-        }
-    }
+    sample_loop<R, D, FN, ADAPT>((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x, a.n,
+                                 (unsigned long long)gridDim.x * blockDim.x, a.iter, 0u, a.rk0,
+                                 a.rk1, a.fc, N, logr,
+                                 (R)(sizeof(R) == 4 ? a.fc.C32 : a.fc.C), n4, nlast, sgrid,
+                                 shist, acc, bad);
 
     const double b1 = block_sum(acc.sum1(), sred);
     const double b2 = block_sum(acc.sum2(), sred);
     const unsigned bb = block_sum(bad, sbad);
     if (ADAPT) {
         __syncthreads();
-        for (int idx = threadIdx.x; idx < D * N; idx += blockDim.x) {
-            const H v = shist[idx];
-            if (v != H(0)) atomicAdd(&a.hist[idx], (double)v);
-        }
+        flush_hist(shist, D * N, logr, 1.0, a.hist);
     }
     if (threadIdx.x == 0) {
         double* p = a.partials + (size_t)blockIdx.x * kPartialStride;
@@ -271,7 +227,8 @@ extern "C" int vegas_iterate_noalloc(double* d_edges, int dim, int nbins, uint64
 
     const bool ad = adapt != 0;
     const void* kern = noalloc_kernel(mode, dim, ad);
-    const size_t smem = iterate_smem_bytes(mode, dim, nbins, ad);
+    a.log2r = ad ? hist_log2r(mode, dim, nbins) : 0;
+    const size_t smem = iterate_smem_bytes(mode, dim, nbins, ad, a.log2r);
     if (smem > 40 * 1024 &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)

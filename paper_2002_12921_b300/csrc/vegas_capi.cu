@@ -44,10 +44,17 @@ const void* iterate_kernel_f64(int integrand, int dim, bool adapt) {
     }
 }
 
-size_t iterate_smem_bytes(int mode, int dim, int nbins, bool adapt) {
+int hist_log2r(int mode, int dim, int nbins) {
+    const size_t hist = mode == VEGAS_FP32_EVAL ? sizeof(float) : sizeof(double);
+    int lr = 5;
+    while (lr > 0 && ((size_t)dim * nbins * hist << lr) > kHistCopyBudget) --lr;
+    return lr;
+}
+
+size_t iterate_smem_bytes(int mode, int dim, int nbins, bool adapt, int log2r) {
     const size_t pair = mode == VEGAS_FP32_EVAL ? 2 * sizeof(float) : 2 * sizeof(double);
     const size_t hist = mode == VEGAS_FP32_EVAL ? sizeof(float) : sizeof(double);
-    return (size_t)dim * nbins * (pair + (adapt ? hist : 0));
+    return (size_t)dim * nbins * (pair + (adapt ? hist << log2r : 0));
 }
 }  // namespace vegas
 
@@ -305,7 +312,8 @@ int vegas_iterate(vegas_state* s, uint64_t n_samples, int adapt) {
     const bool ad = adapt != 0;
     const void* kern = kernel_for(s, ad);
     if (!kern) return VEGAS_EINVAL;
-    const size_t smem = iterate_smem_bytes(s->mode, s->dim, s->nbins, ad);
+    const int log2r = ad ? hist_log2r(s->mode, s->dim, s->nbins) : 0;
+    const size_t smem = iterate_smem_bytes(s->mode, s->dim, s->nbins, ad, log2r);
     // static shared memory (~0.5 KB) counts against the 48 KB default as well
     if (smem > 40 * 1024) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -338,6 +346,7 @@ int vegas_iterate(vegas_state* s, uint64_t n_samples, int adapt) {
     a.n_total = n_samples;
     a.nbins = s->nbins;
     a.max_iters = s->max_iters;
+    a.hist_log2r = log2r;
     a.integral_id = 0;
     std::memcpy(a.rk0, s->rk0, sizeof(a.rk0));
     std::memcpy(a.rk1, s->rk1, sizeof(a.rk1));

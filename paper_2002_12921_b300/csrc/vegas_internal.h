@@ -48,6 +48,7 @@ struct IterArgs {
     unsigned long long n_total;  // samples of the whole iteration
     int first_chunk, last_chunk;
     int nbins, max_iters;
+    int hist_log2r;       // log2 of the number of shared histogram copies
     unsigned integral_id;
     unsigned rk0[10], rk1[10];  // Philox round keys k + r W
     FnConsts fc;
@@ -64,8 +65,12 @@ struct RefineArgs {
 // nullptr.
 const void* iterate_kernel_f32(int integrand, int dim, bool adapt);
 const void* iterate_kernel_f64(int integrand, int dim, bool adapt);
-// dynamic shared memory of an iterate kernel
-size_t iterate_smem_bytes(int mode, int dim, int nbins, bool adapt);
+// Shared histogram copies of an adapting iterate block, as log2: 32 copies
+// (one per lane) where they fit in kHistCopyBudget bytes, fewer otherwise.
+constexpr size_t kHistCopyBudget = 52 * 1024;
+int hist_log2r(int mode, int dim, int nbins);
+// dynamic shared memory of an iterate kernel with 2^log2r histogram copies
+size_t iterate_smem_bytes(int mode, int dim, int nbins, bool adapt, int log2r);
 
 cudaError_t launch_refine(const RefineArgs& a, cudaStream_t stream);
 cudaError_t launch_init(double* edges, double* hist, double* log, unsigned* ctrl, int dim,
