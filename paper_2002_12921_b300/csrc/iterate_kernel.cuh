@@ -26,7 +26,18 @@
 #include "philox.cuh"
 #include "vegas_internal.h"
 
+// launch-shape tuning: minimum resident blocks the register allocation
+// targets, and samples per unrolled loop step
+#ifndef VEGAS_ITERATE_MIN_BLOCKS
+#define VEGAS_ITERATE_MIN_BLOCKS 1
+#endif
+#ifndef VEGAS_SAMPLE_UNROLL
+#define VEGAS_SAMPLE_UNROLL 1
+#endif
+
 namespace vegas {
+
+constexpr int kSampleUnroll = VEGAS_SAMPLE_UNROLL;
 
 // 2^x with the hardware exponential (flush-to-zero for tiny results).
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -36,35 +47,33 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 // ------------------------------------------------------------------------
-// Integrands.  begin() resets the running state, add(k, x) folds in
-// dimension k (a compile-time constant once the kernel's loops are unrolled,
-// so the constants come straight from the parameter bank), value() returns f
-// without its constant prefactor (which the kernel folds into the Jacobian).
+// Integrands, written in the staged coordinate z_k = sc_k x_k + sh_k (see
+// FnConsts).  begin() resets the running state, add(k, z) folds in dimension k
+// (a compile-time constant once the kernel's loops are unrolled, so the
+// constants come straight from the parameter bank), value() returns f without
+// its constant prefactor (which the kernel folds into the Jacobian).
 // ------------------------------------------------------------------------
 template <typename R, int FN>
 struct Integrand;
 
-// Eq. 1, float: s = sum_k ((x_k - mu_k) kappa)^2 with kappa^2 = log2(e)/a^2, f ~ 2^-s.
+// Eq. 1, float: z = kappa (x - mu), kappa^2 = log2(e)/a^2, f ~ 2^(-sum z^2).
 template <>
 struct Integrand<float, VEGAS_GAUSS> {
     float s;
     __device__ __forceinline__ void begin() { s = 0.f; }
-    __device__ __forceinline__ void add(int k, float x, const FnConsts& c) {
-        const float u = fmaf(x, c.kappa, c.q0[k]);
-        s = fmaf(u, u, s);
-    }
+    __device__ __forceinline__ void add(int, float z, const FnConsts&) { s = fmaf(z, z, s); }
     __device__ __forceinline__ float value(const FnConsts&) const { return ex2_approx(-s); }
 };
 
+// two-peak mixture, float: z_B = z_A + kappa (mu_A - mu_B).
 template <>
 struct Integrand<float, VEGAS_GAUSS_MIX2> {
     float sa, sb;
     __device__ __forceinline__ void begin() { sa = 0.f; sb = 0.f; }
-    __device__ __forceinline__ void add(int k, float x, const FnConsts& c) {
-        const float ua = fmaf(x, c.kappa, c.q0[k]);
-        const float ub = fmaf(x, c.kappa, c.q1[k]);
-        sa = fmaf(ua, ua, sa);
-        sb = fmaf(ub, ub, sb);
+    __device__ __forceinline__ void add(int k, float z, const FnConsts& c) {
+        const float zb = z + c.d32[k];
+        sa = fmaf(z, z, sa);
+        sb = fmaf(zb, zb, sb);
     }
     __device__ __forceinline__ float value(const FnConsts&) const {
         return ex2_approx(-sa) + ex2_approx(-sb);
@@ -78,58 +87,51 @@ struct Integrand<float, VEGAS_FLAT> {
     __device__ __forceinline__ float value(const FnConsts&) const { return 1.f; }
 };
 
-// Eq. 2, float: q0 = a_k (threshold), q1 = c_k log2(e).
+// Eq. 2, float: z = x; zero unless every x_k > a_k, else 2^(sum c_k log2(e) x_k).
 template <>
 struct Integrand<float, VEGAS_GENZ_DISC> {
     float s;
     bool inside;
     __device__ __forceinline__ void begin() { s = 0.f; inside = true; }
-    __device__ __forceinline__ void add(int k, float x, const FnConsts& c) {
-        s = fmaf(x, c.q1[k], s);
-        inside = inside && (x > c.q0[k]);
+    __device__ __forceinline__ void add(int k, float z, const FnConsts& c) {
+        s = fmaf(z, c.d32[k], s);
+        inside = inside && (z > c.t32[k]);
     }
     __device__ __forceinline__ float value(const FnConsts&) const {
         return inside ? ex2_approx(s) : 0.f;
     }
 };
 
-// Eq. 3, float: 1/(c^-2 + u^2) = c^2 / (1 + (c u)^2); q1 = c_k, q0 = -a_k c_k;
-// the c_k^2 and the normalisation sit in the prefactor.
+// Eq. 3, float: z = c (x - a), each factor c^2 / (1 + z^2); the c^2 and the
+// normalisation sit in the prefactor.
 template <>
 struct Integrand<float, VEGAS_GENZ_PPEAK> {
     float p;
     __device__ __forceinline__ void begin() { p = 1.f; }
-    __device__ __forceinline__ void add(int k, float x, const FnConsts& c) {
-        const float t = fmaf(x, c.q1[k], c.q0[k]);
-        p *= fmaf(t, t, 1.f);
-    }
+    __device__ __forceinline__ void add(int, float z, const FnConsts&) { p *= fmaf(z, z, 1.f); }
     __device__ __forceinline__ float value(const FnConsts&) const { return __fdividef(1.f, p); }
 };
 
-// Eq. 1, double: exp(-sum (x_k - mu_k)^2 / a^2).
+// Eq. 1, double: z = (x - mu)/a, f ~ exp(-sum z^2).
 template <>
 struct Integrand<double, VEGAS_GAUSS> {
     double s;
     __device__ __forceinline__ void begin() { s = 0.0; }
-    __device__ __forceinline__ void add(int k, double x, const FnConsts& c) {
-        const double u = x - c.p0[k];
-        s = fma(u, u, s);
-    }
-    __device__ __forceinline__ double value(const FnConsts& c) const { return exp(-s * c.inv_a2); }
+    __device__ __forceinline__ void add(int, double z, const FnConsts&) { s = fma(z, z, s); }
+    __device__ __forceinline__ double value(const FnConsts&) const { return exp(-s); }
 };
 
 template <>
 struct Integrand<double, VEGAS_GAUSS_MIX2> {
     double sa, sb;
     __device__ __forceinline__ void begin() { sa = 0.0; sb = 0.0; }
-    __device__ __forceinline__ void add(int k, double x, const FnConsts& c) {
-        const double ua = x - c.p0[k];
-        const double ub = x - c.p1[k];
-        sa = fma(ua, ua, sa);
-        sb = fma(ub, ub, sb);
+    __device__ __forceinline__ void add(int k, double z, const FnConsts& c) {
+        const double zb = z + c.d64[k];
+        sa = fma(z, z, sa);
+        sb = fma(zb, zb, sb);
     }
-    __device__ __forceinline__ double value(const FnConsts& c) const {
-        return exp(-sa * c.inv_a2) + exp(-sb * c.inv_a2);
+    __device__ __forceinline__ double value(const FnConsts&) const {
+        return exp(-sa) + exp(-sb);
     }
 };
 
@@ -140,41 +142,39 @@ struct Integrand<double, VEGAS_FLAT> {
     __device__ __forceinline__ double value(const FnConsts&) const { return 1.0; }
 };
 
-// Eq. 2, double: p0 = a_k, p1 = c_k.
+// Eq. 2, double: z = x.
 template <>
 struct Integrand<double, VEGAS_GENZ_DISC> {
     double s;
     bool inside;
     __device__ __forceinline__ void begin() { s = 0.0; inside = true; }
-    __device__ __forceinline__ void add(int k, double x, const FnConsts& c) {
-        s = fma(c.p1[k], x, s);
-        inside = inside && (x > c.p0[k]);
+    __device__ __forceinline__ void add(int k, double z, const FnConsts& c) {
+        s = fma(c.d64[k], z, s);
+        inside = inside && (z > c.t64[k]);
     }
     __device__ __forceinline__ double value(const FnConsts&) const {
         return inside ? exp(s) : 0.0;
     }
 };
 
-// Eq. 3, double: p0 = a_k, p1 = c_k^-2; f ~ 1 / prod_k (c_k^-2 + (x_k - a_k)^2).
+// Eq. 3, double: z = c (x - a), f ~ 1 / prod_k (1 + z_k^2).
 template <>
 struct Integrand<double, VEGAS_GENZ_PPEAK> {
     double p;
     __device__ __forceinline__ void begin() { p = 1.0; }
-    __device__ __forceinline__ void add(int k, double x, const FnConsts& c) {
-        const double u = x - c.p0[k];
-        p *= fma(u, u, c.p1[k]);
-    }
+    __device__ __forceinline__ void add(int, double z, const FnConsts&) { p *= fma(z, z, 1.0); }
     __device__ __forceinline__ double value(const FnConsts&) const { return 1.0 / p; }
 };
 
 // ------------------------------------------------------------------------
 // Precision-specific pieces of the map.  unit(l) is the number in [1, 2) whose
-// mantissa holds the position bits; the staged pair is (e - (1 - u/2) Delta,
-// Delta) with u the unit's spacing, so that x = fma(unit, Delta, e') is
-// e + frac Delta with frac = unit - (1 - u/2) in (0, 1): for float,
-// frac = (floor(l / 2^9) + 1/2) 2^-23; for double, frac = (l + 1/2) 2^-32.
-// Folding the offset into the staged edge saves one add per dimension; it moves
-// x by at most an ulp of the edge.
+// mantissa holds the position bits.  The staged pair of a bin is
+// (sc e' + sh, sc Delta) with e' = e - (1 - u/2) Delta (u the unit's spacing),
+// so that z = fma(unit, sc Delta, sc e' + sh) = sc (e + frac Delta) + sh with
+// frac = unit - (1 - u/2) in (0, 1): for float frac = (floor(l / 2^9) + 1/2)
+// 2^-23, for double frac = (l + 1/2) 2^-32.  One fused multiply-add gives the
+// integrand's coordinate; the staged values are rounded once, which moves z by
+// at most an ulp.
 // ------------------------------------------------------------------------
 template <typename R>
 struct Prec;
@@ -187,10 +187,12 @@ struct Prec<float> {
         // (0x7F : l) >> 9 = 0x3F800000 | (l >> 9): one funnel shift
         return __uint_as_float(__funnelshift_r(l, 0x7Fu, 9));
     }
-    static __device__ __forceinline__ Pair pair(double e0, double e1) {
-        const float f0 = (float)e0, f1 = (float)e1;
-        const float w = f1 - f0;
-        return make_float2(fmaf(-0x1.fffffep-1f, w, f0), w);
+    static constexpr int kStage = 1;  // FnConsts staging index
+    // (sc e' + sh, sc Delta) computed in double, rounded once
+    static __device__ __forceinline__ Pair pair(double e0, double e1, double sc, double sh) {
+        const double w = e1 - e0;
+        const double e = ::fma(-0x1.fffffep-1, w, e0);
+        return make_float2((float)::fma(e, sc, sh), (float)(w * sc));
     }
     static __device__ __forceinline__ bool finite(float v) { return fabsf(v) <= FLT_MAX; }
     static __device__ __forceinline__ float fma(float x, float y, float z) { return fmaf(x, y, z); }
@@ -204,9 +206,11 @@ struct Prec<double> {
         // high word (0x3FF : l) >> 12 = 0x3FF00000 | (l >> 12), low word l << 20
         return __hiloint2double((int)__funnelshift_r(l, 0x3FFu, 12), (int)(l << 20));
     }
-    static __device__ __forceinline__ Pair pair(double e0, double e1) {
+    static constexpr int kStage = 0;
+    static __device__ __forceinline__ Pair pair(double e0, double e1, double sc, double sh) {
         const double w = e1 - e0;
-        return make_double2(::fma(-0x1.ffffffffp-1, w, e0), w);
+        const double e = ::fma(-0x1.ffffffffp-1, w, e0);
+        return make_double2(::fma(e, sc, sh), w * sc);
     }
     static __device__ __forceinline__ bool finite(double v) { return fabs(v) <= DBL_MAX; }
     static __device__ __forceinline__ double fma(double x, double y, double z) {
@@ -247,8 +251,7 @@ struct Acc<float> {
         const float t1 = s1 + y1;
         c1 = (t1 - s1) - y1;
         s1 = t1;
-        const float v2 = __fmul_rn(v, v);
-        const float y2 = v2 - c2;
+        const float y2 = fmaf(v, v, -c2);  // v^2 - c2 with one rounding
         const float t2 = s2 + y2;
         c2 = (t2 - s2) - y2;
         s2 = t2;
@@ -280,13 +283,13 @@ struct Acc<double> {
 // ------------------------------------------------------------------------
 template <typename R, int D, bool ADAPT>
 __device__ __forceinline__ void stage_grid(const double* __restrict__ edges, int N, int logr,
-                                           typename Prec<R>::Pair* sgrid,
+                                           const FnConsts& fc, typename Prec<R>::Pair* sgrid,
                                            typename Prec<R>::Hist* shist) {
     using P = Prec<R>;
     for (int idx = threadIdx.x; idx < D * N; idx += blockDim.x) {
         const int k = idx / N, j = idx - k * N;
         const double* e = edges + (size_t)k * (N + 1) + j;
-        sgrid[idx] = P::pair(e[0], e[1]);
+        sgrid[idx] = P::pair(e[0], e[1], fc.sc[P::kStage][k], fc.sh[P::kStage][k]);
     }
     if (ADAPT)
         for (int idx = threadIdx.x; idx < (D * N) << logr; idx += blockDim.x)
@@ -309,15 +312,34 @@ __device__ __forceinline__ void sample_loop(unsigned long long first, unsigned l
     using H = typename P::Hist;
     constexpr int DC = (D + 3) / 4;  // Philox calls per sample
     const int lane_copy = threadIdx.x & ((1 << logr) - 1);
+    // per-call constants of the shared first two Philox rounds, for the
+    // current high word of the sample index
+    const uint32_t t_key = it ^ rk1[0];
+    uint32_t cur_hi = (uint32_t)(first >> 32);
+    PhiloxCallConst pc[DC];
+#pragma unroll
+    for (int q = 0; q < DC; ++q) pc[q] = philox_call_const(c2base | (uint32_t)q, cur_hi, rk0, rk1);
+#pragma unroll kSampleUnroll
     for (unsigned long long i = first; i < end; i += stride) {
+        const uint32_t i_lo = (uint32_t)i, i_hi = (uint32_t)(i >> 32);
+        if (i_hi != cur_hi) {  // crossing a multiple of 2^32: rare
+            cur_hi = i_hi;
+#pragma unroll
+            for (int q = 0; q < DC; ++q) pc[q] = philox_call_const(c2base | (uint32_t)q, i_hi, rk0, rk1);
+        }
+        // rounds 0 and 1, shared by the calls: two wide multiplies per sample
+        const uint32_t lo0 = kPhiloxM0 * i_lo;
+        const uint32_t w2r0 = __umulhi(kPhiloxM0, i_lo) ^ t_key;
+        const uint32_t hi1 = __umulhi(kPhiloxM1, w2r0);
+        const uint32_t lo1 = kPhiloxM1 * w2r0;
         Integrand<R, FN> f;
         f.begin();
         R J = jstart;
         int hb[D];
 #pragma unroll
         for (int q = 0; q < DC; ++q) {
-            uint32_t w0 = (uint32_t)i, w1 = (uint32_t)(i >> 32), w2 = c2base | (uint32_t)q, w3 = it;
-            philox4x32_10(w0, w1, w2, w3, rk0, rk1);
+            uint32_t w0 = hi1 ^ pc[q].a, w1 = lo1, w2 = lo0 ^ pc[q].b, w3 = pc[q].c;
+            philox_rounds<2, 10>(w0, w1, w2, w3, rk0, rk1);
             const uint32_t w[4] = {w0, w1, w2, w3};
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
@@ -375,7 +397,8 @@ __device__ __forceinline__ void jacobian_factors(int N, R& n4, R& nlast) {
 // accumulate the refinement histogram.
 // ------------------------------------------------------------------------
 template <typename R, int D, int FN, bool ADAPT>
-__global__ void __launch_bounds__(256) vegas_iterate_kernel(const IterArgs a) {
+__global__ void __launch_bounds__(256, VEGAS_ITERATE_MIN_BLOCKS)
+    vegas_iterate_kernel(const IterArgs a) {
     using P = Prec<R>;
     using Pair = typename P::Pair;
     using H = typename P::Hist;
@@ -395,7 +418,7 @@ __global__ void __launch_bounds__(256) vegas_iterate_kernel(const IterArgs a) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctrl[kStatus], kStatusLogFull);
         return;
     }
-    stage_grid<R, D, ADAPT>(a.edges, N, logr, sgrid, shist);
+    stage_grid<R, D, ADAPT>(a.edges, N, logr, a.fc, sgrid, shist);
 
     // Pre-scale of the float path: f J is carried as f J 2^-h with 2^h near the
     // previous iteration's estimate; the prefactor enters the Jacobian's start.

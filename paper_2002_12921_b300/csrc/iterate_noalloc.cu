@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) noalloc_iterate_kernel(const NoAllocArgs 
     const int logr = ADAPT ? a.log2r : 0;
     Pair* sgrid = reinterpret_cast<Pair*>(smem_raw);
     H* shist = reinterpret_cast<H*>(sgrid + D * N);
-    stage_grid<R, D, ADAPT>(a.edges, N, logr, sgrid, shist);
+    stage_grid<R, D, ADAPT>(a.edges, N, logr, a.fc, sgrid, shist);
     R n4, nlast;
     jacobian_factors<R, D>(N, n4, nlast);
     __syncthreads();
@@ -195,19 +195,11 @@ extern "C" int vegas_iterate_noalloc(double* d_edges, int dim, int nbins, uint64
     if (scratch_address(attr.device, &scratch) != cudaSuccess) return VEGAS_ECUDA;
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
 
-    // Gaussian constants (Eq. 1): (a sqrt(pi))^-d, with N^d for the FP64 Jacobian
+    // Gaussian constants (Eq. 1), as for the workspace path
     NoAllocArgs a;
     std::memset(&a, 0, sizeof(a));
-    const double norm = std::pow(a_width * std::sqrt(M_PI), -(double)dim);
-    const double kappa = std::sqrt(1.4426950408889634) / a_width;
-    a.fc.C = norm * std::pow((double)nbins, dim);
-    a.fc.C32 = norm;
-    a.fc.inv_a2 = 1.0 / (a_width * a_width);
-    a.fc.kappa = (float)kappa;
-    for (int k = 0; k < dim; ++k) {
-        a.fc.p0[k] = params[1 + k];
-        a.fc.q0[k] = (float)(-params[1 + k] * kappa);
-    }
+    if (make_consts(VEGAS_GAUSS, dim, nbins, params, nparams, &a.fc) != VEGAS_OK)
+        return VEGAS_EINVAL;
     philox_round_keys(seed, a.rk0, a.rk1);
     a.edges = d_edges;
     a.hist = reinterpret_cast<double*>(scratch + kNaHist);

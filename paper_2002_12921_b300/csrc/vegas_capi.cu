@@ -56,6 +56,94 @@ size_t iterate_smem_bytes(int mode, int dim, int nbins, bool adapt, int log2r) {
     const size_t hist = mode == VEGAS_FP32_EVAL ? sizeof(float) : sizeof(double);
     return (size_t)dim * nbins * (pair + (adapt ? hist << log2r : 0));
 }
+
+namespace {
+bool finite_params(const double* p, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+}  // namespace
+
+// Integrand constants for both precisions (see FnConsts).  Index 0 of the
+// staging transform is the double path, index 1 the float path.
+int make_consts(int integrand, int dim, int nbins, const double* params, int nparams,
+                FnConsts* fc) {
+    std::memset(fc, 0, sizeof(*fc));
+    const double log2e = 1.4426950408889634;
+    const double npow = std::pow((double)nbins, dim);  // N^dim of the FP64 Jacobian
+    for (int k = 0; k < dim; ++k) fc->sc[0][k] = fc->sc[1][k] = 1.0;
+    switch (integrand) {
+    case VEGAS_GAUSS:
+    case VEGAS_GAUSS_MIX2: {
+        const int need = integrand == VEGAS_GAUSS ? 1 + dim : 1 + 2 * dim;
+        if (!params || nparams < need || !finite_params(params, need)) return VEGAS_EINVAL;
+        const double a = params[0];
+        if (!(a > 0.0)) return VEGAS_EINVAL;
+        // (a sqrt(pi))^-d, halved for the two-term mixture
+        double norm = std::pow(a * std::sqrt(M_PI), -(double)dim);
+        if (integrand == VEGAS_GAUSS_MIX2) norm *= 0.5;
+        // double: z = (x - mu)/a, f ~ exp(-sum z^2); float: z = kappa (x - mu),
+        // kappa^2 = log2(e)/a^2, f ~ 2^(-sum z^2)
+        const double kappa = std::sqrt(log2e) / a;
+        for (int k = 0; k < dim; ++k) {
+            const double mu = params[1 + k];
+            fc->sc[0][k] = 1.0 / a;
+            fc->sh[0][k] = -mu / a;
+            fc->sc[1][k] = kappa;
+            fc->sh[1][k] = -mu * kappa;
+            if (integrand == VEGAS_GAUSS_MIX2) {
+                const double dmu = mu - params[1 + dim + k];  // z_B = z_A + (mu_A - mu_B) sc
+                fc->d64[k] = dmu / a;
+                fc->d32[k] = (float)(dmu * kappa);
+            }
+        }
+        fc->C = norm * npow * std::pow(a, dim);
+        fc->C32 = norm / std::pow(kappa, dim);
+        return VEGAS_OK;
+    }
+    case VEGAS_FLAT:
+        fc->C = npow;
+        fc->C32 = 1.0;
+        return VEGAS_OK;
+    case VEGAS_GENZ_DISC: {
+        if (!params || nparams < 2 * dim || !finite_params(params, 2 * dim)) return VEGAS_EINVAL;
+        double norm = 1.0;  // prod_k (e^{c_k} - e^{c_k a_k}) / c_k
+        for (int k = 0; k < dim; ++k) {
+            const double ak = params[k], ck = params[dim + k];
+            if (ck == 0.0) return VEGAS_EINVAL;
+            norm *= (std::exp(ck) - std::exp(ck * ak)) / ck;
+            fc->t64[k] = ak;
+            fc->d64[k] = ck;
+            fc->t32[k] = (float)ak;
+            fc->d32[k] = (float)(ck * log2e);
+        }
+        if (!(norm > 0.0) || !std::isfinite(norm)) return VEGAS_EINVAL;
+        fc->C = npow / norm;
+        fc->C32 = 1.0 / norm;
+        return VEGAS_OK;
+    }
+    case VEGAS_GENZ_PPEAK: {
+        if (!params || nparams < 2 * dim || !finite_params(params, 2 * dim)) return VEGAS_EINVAL;
+        // z = c (x - a): 1/(c^-2 + (x-a)^2) = c^2/(1 + z^2); with the staging's
+        // 1/prod c the prefactor is prod_k c_k / integral_k
+        double pref = 1.0;
+        for (int k = 0; k < dim; ++k) {
+            const double ak = params[k], ck = params[dim + k];
+            if (!(ck > 0.0)) return VEGAS_EINVAL;
+            const double integral = ck * (std::atan(ck * (1.0 - ak)) + std::atan(ck * ak));
+            pref *= ck / integral;
+            fc->sc[0][k] = fc->sc[1][k] = ck;
+            fc->sh[0][k] = fc->sh[1][k] = -ak * ck;
+        }
+        fc->C = pref * npow;
+        fc->C32 = pref;
+        return VEGAS_OK;
+    }
+    default:
+        return VEGAS_EINVAL;
+    }
+}
 }  // namespace vegas
 
 using namespace vegas;
@@ -124,87 +212,6 @@ struct DeviceGuard {
         if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
     }
 };
-
-bool finite_all(const double* p, int n) {
-    for (int i = 0; i < n; ++i)
-        if (!std::isfinite(p[i])) return false;
-    return true;
-}
-
-// Integrand constants for both precisions (see FnConsts).
-int make_consts(int integrand, int dim, int nbins, const double* params, int nparams,
-                FnConsts* fc) {
-    std::memset(fc, 0, sizeof(*fc));
-    const double log2e = 1.4426950408889634;
-    const double npow = std::pow((double)nbins, dim);  // N^dim of the FP64 Jacobian
-    switch (integrand) {
-    case VEGAS_GAUSS:
-    case VEGAS_GAUSS_MIX2: {
-        const int need = integrand == VEGAS_GAUSS ? 1 + dim : 1 + 2 * dim;
-        if (!params || nparams < need || !finite_all(params, need)) return VEGAS_EINVAL;
-        const double a = params[0];
-        if (!(a > 0.0)) return VEGAS_EINVAL;
-        // (a sqrt(pi))^-d, halved for the two-term mixture
-        double norm = std::pow(a * std::sqrt(M_PI), -(double)dim);
-        if (integrand == VEGAS_GAUSS_MIX2) norm *= 0.5;
-        fc->C = norm * npow;
-        fc->C32 = norm;
-        fc->inv_a2 = 1.0 / (a * a);
-        const double kappa = std::sqrt(log2e) / a;
-        fc->kappa = (float)kappa;
-        for (int k = 0; k < dim; ++k) {
-            fc->p0[k] = params[1 + k];
-            fc->q0[k] = (float)(-params[1 + k] * kappa);
-            if (integrand == VEGAS_GAUSS_MIX2) {
-                fc->p1[k] = params[1 + dim + k];
-                fc->q1[k] = (float)(-params[1 + dim + k] * kappa);
-            }
-        }
-        return VEGAS_OK;
-    }
-    case VEGAS_FLAT:
-        fc->C = npow;
-        fc->C32 = 1.0;
-        return VEGAS_OK;
-    case VEGAS_GENZ_DISC: {
-        if (!params || nparams < 2 * dim || !finite_all(params, 2 * dim)) return VEGAS_EINVAL;
-        double norm = 1.0;  // prod_k (e^{c_k} - e^{c_k a_k}) / c_k
-        for (int k = 0; k < dim; ++k) {
-            const double ak = params[k], ck = params[dim + k];
-            if (ck == 0.0) return VEGAS_EINVAL;
-            norm *= (std::exp(ck) - std::exp(ck * ak)) / ck;
-            fc->p0[k] = ak;
-            fc->p1[k] = ck;
-            fc->q0[k] = (float)ak;
-            fc->q1[k] = (float)(ck * log2e);
-        }
-        if (!(norm > 0.0) || !std::isfinite(norm)) return VEGAS_EINVAL;
-        fc->C = npow / norm;
-        fc->C32 = 1.0 / norm;
-        return VEGAS_OK;
-    }
-    case VEGAS_GENZ_PPEAK: {
-        if (!params || nparams < 2 * dim || !finite_all(params, 2 * dim)) return VEGAS_EINVAL;
-        double inv_int = 1.0;   // prod_k 1/(c_k (atan(c_k (1-a_k)) + atan(c_k a_k)))
-        double c2 = 1.0;        // prod_k c_k^2
-        for (int k = 0; k < dim; ++k) {
-            const double ak = params[k], ck = params[dim + k];
-            if (!(ck > 0.0)) return VEGAS_EINVAL;
-            inv_int /= ck * (std::atan(ck * (1.0 - ak)) + std::atan(ck * ak));
-            c2 *= ck * ck;
-            fc->p0[k] = ak;
-            fc->p1[k] = 1.0 / (ck * ck);
-            fc->q0[k] = (float)(-ak * ck);
-            fc->q1[k] = (float)ck;
-        }
-        fc->C = inv_int * npow;
-        fc->C32 = inv_int * c2;
-        return VEGAS_OK;
-    }
-    default:
-        return VEGAS_EINVAL;
-    }
-}
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? VEGAS_OK : VEGAS_ECUDA; }
 

@@ -23,18 +23,25 @@ enum CtrlWord { kTicket = 0, kIter = 1, kStatus = 2, kCtrlWords = 64 };
 enum StatusBit { kStatusLogFull = 1u };
 
 // Integrand constants, precomputed on the host from the user's parameters.
+//
+// Staging transform: every bin is staged in the integrand's own coordinate
+// z_k = sc_k x_k + sh_k (per precision: index 0 double, 1 float), so the map
+// yields z with one fused multiply-add.  The Jacobian then collects
+// prod_k N Delta_k sc_k, and 1/prod_k sc_k is folded into the prefactors.
 struct FnConsts {
-    // double-precision path
-    double C;        // prefactor: normalisation times N^dim (the FP64 Jacobian's N factors)
-    double inv_a2;   // GAUSS, MIX2: 1/a^2
-    double p0[kMaxDim];  // GAUSS, MIX2: centre A; GENZ: a_k
-    double p1[kMaxDim];  // MIX2: centre B; GENZ_DISC: c_k; GENZ_PPEAK: c_k^-2
-    // single-precision path (the prefactor C32 is applied in double per block)
-    double C32;      // prefactor for the FP32 path (without N^dim)
-    float kappa;     // GAUSS, MIX2: sqrt(log2 e)/a
-    float q0[kMaxDim];   // GAUSS, MIX2: -mu_A kappa; GENZ_DISC: a_k; GENZ_PPEAK: -a_k c_k
-    float q1[kMaxDim];   // MIX2: -mu_B kappa; GENZ_DISC: c_k log2 e; GENZ_PPEAK: c_k
+    double C;        // FP64 prefactor: normalisation x N^dim / prod sc
+    double C32;      // FP32 prefactor: normalisation / prod sc (N^dim enters in the loop)
+    double sc[2][kMaxDim];  // staging scale per precision and dimension
+    double sh[2][kMaxDim];  // staging shift
+    double d64[kMaxDim];    // MIX2: z_B - z_A in the double coordinate; GENZ_DISC: c_k
+    double t64[kMaxDim];    // GENZ_DISC: thresholds a_k
+    float d32[kMaxDim];     // MIX2: z_B - z_A in the float coordinate; GENZ_DISC: c_k log2 e
+    float t32[kMaxDim];     // GENZ_DISC: thresholds a_k
 };
+
+// Fill FnConsts for an integrand (VEGAS_EINVAL on bad parameters).
+int make_consts(int integrand, int dim, int nbins, const double* params, int nparams,
+                FnConsts* fc);
 
 // Arguments of one iterate launch (passed by value in the parameter bank).
 struct IterArgs {
