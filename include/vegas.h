@@ -169,6 +169,24 @@ int vegas_get_histogram(vegas_state *s, double *host_hist);
 int vegas_sample_words(uint64_t seed, uint32_t integral_id, uint32_t iter, uint64_t i0,
                        uint64_t n, int dim, uint32_t *d_out, void *cuda_stream);
 
+/* Gradient of the Eq. 1 Gaussian integral with respect to its parameters, by
+ * the reparameterised fixed-grid estimator: on the state's current (frozen)
+ * grid, sample i of iteration `iter` is regenerated from its Philox counter
+ * (nothing per sample is stored), and
+ *   I = (1/n) sum_i f(x_i) J_i,   dI/dtheta = (1/n) sum_i J_i df/dtheta(x_i),
+ * with df/dmu_k = f 2 (x_k - mu_k)/a^2 and df/da = (f/a)(2 sum_k (x_k-mu_k)^2/a^2 - d).
+ * params = [a, mu_1 .. mu_d] (as VEGAS_GAUSS; independent of the state's own
+ * integrand).  d_out: 2 (dim+2) + 1 device doubles owned by the caller:
+ * [I, dI/dmu_1 .. dI/dmu_d, dI/da, then the Monte Carlo variances of those
+ * d+2 means, then the count of non-finite weights].  grad == 0 computes only
+ * I and its variance (the other entries are set to 0).  Uses the state's
+ * mode, seed, grid, workspace and stream; the same (iter, n) as an earlier
+ * vegas_iterate on the same grid reproduces its samples exactly.
+ * Asynchronous.  The paper's integrator has no gradient; this is the
+ * differentiable extension of the same estimator. */
+int vegas_gauss_adjoint(vegas_state *s, const double *params, int nparams, uint32_t iter,
+                        uint64_t n_samples, int grad, double *d_out);
+
 /* ---- entry point for callers that cannot allocate device memory ---------- */
 /* The paper has no counterpart to this call; it exists for callers that are not
  * allowed to allocate device memory -- code that runs inside a host framework

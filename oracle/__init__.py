@@ -48,6 +48,8 @@ def lib():
         L.oracle_refine.restype = i32
         L.oracle_combine.argtypes = [i32, vp, vp, vp, vp, vp]
         L.oracle_combine.restype = None
+        L.oracle_gauss_gradient.argtypes = [i32, i32, vp, u64, u32, u64, vp, vp]
+        L.oracle_gauss_gradient.restype = i32
         L.oracle_uniform_grid.argtypes = [i32, i32, vp]
         L.oracle_uniform_grid.restype = None
         _lib = L
@@ -160,6 +162,22 @@ def combine(I, var):
     out = np.zeros(3)
     lib().oracle_combine(len(I), _ptr(I), _ptr(var), _ptr(out[0:]), _ptr(out[1:]), _ptr(out[2:]))
     return float(out[0]), float(out[1]), float(out[2])
+
+
+def gauss_gradient(edges, seed, it, n, params):
+    """Fixed-grid estimate of the Eq. 1 integral and its gradient in
+    (mu_1..mu_d, a) over samples 0..n-1 of iteration it: dict(I, dmu, da,
+    var_I, var_dmu, var_da, nonfinite)."""
+    edges = _c(edges, np.float64)
+    dim, nb1 = edges.shape
+    p = _c(params, np.float64)
+    out = np.zeros(2 * (dim + 2) + 1)
+    if lib().oracle_gauss_gradient(dim, nb1 - 1, _ptr(edges), seed, it, n, _ptr(p), _ptr(out)):
+        raise ValueError("oracle_gauss_gradient: invalid arguments")
+    nc = dim + 2
+    return dict(I=out[0], dmu=out[1:dim + 1].copy(), da=out[dim + 1], var_I=out[nc],
+                var_dmu=out[nc + 1:nc + 1 + dim].copy(), var_da=out[nc + dim + 1],
+                nonfinite=int(out[2 * nc]), raw=out)
 
 
 def run(dim, nbins, seed, fid, params, schedule, alpha=1.5, integral_id=0, nthreads=1,

@@ -21,6 +21,8 @@
  *   6. per-dimension per-bin histogram of (fJ)^2              (oracle_iterate)
  *   7. smoothing, damping and equal-weight re-partition       (oracle_refine)
  *   8. inverse-variance combination of iterations             (oracle_combine)
+ *   9. gradient of the fixed-grid Eq. 1 estimate with respect
+ *      to (mu, a), over the same samples                      (oracle_gauss_gradient)
  *
  * Every floating-point quantity is double; sums are carried in long double so
  * that the oracle's own rounding is far below the parity tolerance.  The file
@@ -29,7 +31,9 @@
  * Pins (in the CPU test suite): Philox words against an independent library
  * implementation; the identity map on a uniform grid; exact results for the
  * constant integrand; closed-form Gaussian integrals; brute-force quadrature
- * at d <= 2; refinement invariants; hand-worked combination examples.
+ * at d <= 2; refinement invariants; hand-worked combination examples; for the
+ * gradient, central finite differences of the estimator and the analytic erf
+ * derivatives of the integral.
  */
 #include <math.h>
 #include <pthread.h>
@@ -457,4 +461,58 @@ void oracle_integrand_batch(uint64_t n, int id, int dim, const double *params, c
                             double *f)
 {
     for (uint64_t i = 0; i < n; ++i) f[i] = oracle_integrand(id, dim, params, x + i * dim);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Gradient of the fixed-grid estimator of Eq. 1 with respect to its          */
+/* parameters.  On a fixed grid the samples do not depend on the parameters,  */
+/* so d/dtheta of (1/n) sum_i f(x_i) J_i is (1/n) sum_i J_i df/dtheta(x_i).    */
+/* For f = (a sqrt(pi))^-d exp(-sum_k (x_k - mu_k)^2 / a^2):                    */
+/*   df/dmu_k = f * 2 (x_k - mu_k) / a^2                                         */
+/*   df/da    = f * (2 sum_k (x_k - mu_k)^2 / a^3 - d / a)                        */
+/* params = [a, mu_1..mu_d].  out: [I, dI/dmu_1..dI/dmu_d, dI/da] then the      */
+/* variances of those d+2 sample means, then the non-finite count.              */
+/* ------------------------------------------------------------------------- */
+int oracle_gauss_gradient(int dim, int nbins, const double *edges, uint64_t seed, uint32_t iter,
+                          uint64_t n, const double *params, double *out)
+{
+    if (dim < 1 || dim > ORACLE_MAX_DIM || n < 2) return -1;
+    const int nc = dim + 2;
+    long double *s1 = calloc((size_t)nc, sizeof(long double));
+    long double *s2 = calloc((size_t)nc, sizeof(long double));
+    double *g = malloc(sizeof(double) * nc);
+    if (!s1 || !s2 || !g) { free(s1); free(s2); free(g); return -1; }
+    const double a = params[0];
+    const double *mu = params + 1;
+    uint32_t words[ORACLE_MAX_DIM];
+    double x[ORACLE_MAX_DIM];
+    uint64_t bad = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        double J;
+        oracle_sample_words(seed, 0, iter, i, dim, words);
+        oracle_map_sample(dim, nbins, edges, words, x, &J, NULL);
+        double fw = gauss_product(dim, a, mu, x) * J;
+        if (!isfinite(fw)) { bad++; continue; }
+        double sq = 0.0;
+        g[0] = fw;
+        for (int k = 0; k < dim; ++k) {
+            double u = x[k] - mu[k];
+            g[1 + k] = fw * 2.0 * u / (a * a);
+            sq += u * u;
+        }
+        g[dim + 1] = fw * (2.0 * sq / (a * a * a) - dim / a);
+        for (int c = 0; c < nc; ++c) {
+            s1[c] += g[c];
+            s2[c] += (long double)g[c] * g[c];
+        }
+    }
+    for (int c = 0; c < nc; ++c) {
+        long double m = s1[c] / (long double)n;
+        long double v = (s2[c] / (long double)n - m * m) / (long double)(n - 1);
+        out[c] = (double)m;
+        out[nc + c] = v > 0 ? (double)v : 0.0;
+    }
+    out[2 * nc] = (double)bad;
+    free(s1); free(s2); free(g);
+    return 0;
 }

@@ -23,7 +23,7 @@ LOG_COLUMNS = ("S1", "S2", "n", "nonfinite", "I", "var")
 EXPORTED = ("vegas_workspace_bytes", "vegas_init_grid", "vegas_set_config", "vegas_iterate",
             "vegas_refine", "vegas_result", "vegas_get_iterations", "vegas_get_grid",
             "vegas_set_grid", "vegas_get_histogram", "vegas_sample_words", "vegas_destroy",
-            "vegas_strerror", "vegas_iterate_noalloc")
+            "vegas_strerror", "vegas_iterate_noalloc", "vegas_gauss_adjoint")
 
 
 class VegasError(RuntimeError):
@@ -67,6 +67,7 @@ def lib():
                                          vp]
         L.vegas_iterate_noalloc.argtypes = [vp, i32, i32, u64, ctypes.c_uint32, i32, vp, i32, u64,
                                              i32, dbl, vp, vp]
+        L.vegas_gauss_adjoint.argtypes = [vp, vp, i32, ctypes.c_uint32, u64, i32, vp]
         L.vegas_destroy.argtypes = [vp]
         L.vegas_strerror.argtypes = [i32]
         L.vegas_strerror.restype = ctypes.c_char_p
@@ -172,6 +173,14 @@ def vegas_iterate_noalloc(d_edges, dim, nbins, seed, it, mode, params, n_samples
            "vegas_iterate_noalloc")
 
 
+def vegas_gauss_adjoint(h, params, it, n_samples, grad, d_out):
+    """Fixed-grid Eq. 1 estimate (and its gradient in (mu, a) when grad) into
+    the device buffer d_out of 2 (dim+2) + 1 doubles (see include/vegas.h)."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    _check(lib().vegas_gauss_adjoint(h, p.ctypes.data, int(p.size), it, int(n_samples),
+                                     1 if grad else 0, d_out), "vegas_gauss_adjoint")
+
+
 def vegas_destroy(h):
     if h:
         _check(lib().vegas_destroy(h), "vegas_destroy")
@@ -216,6 +225,16 @@ class Vegas:
 
     def histogram(self):
         return vegas_get_histogram(self.handle, self.dim, self.nbins)
+
+    def gauss_adjoint(self, params, it, n, grad=True):
+        """(I, dI/dmu, dI/da, variances, nonfinite) on the current grid as a
+        device tensor of 2 (dim+2) + 1 doubles."""
+        import torch
+
+        out = torch.empty(2 * (self.dim + 2) + 1, dtype=torch.float64,
+                          device=self.workspace.device)
+        vegas_gauss_adjoint(self.handle, params, it, n, grad, out.data_ptr())
+        return out
 
     def run(self, schedule, alpha=1.5):
         """Enqueue (n, adapt) iterations; each adapting one is followed by a

@@ -28,8 +28,10 @@
 
 // launch-shape tuning: minimum resident blocks the register allocation
 // targets, and samples per unrolled loop step
-#ifndef VEGAS_ITERATE_MIN_BLOCKS
-#define VEGAS_ITERATE_MIN_BLOCKS 1
+#ifdef VEGAS_ITERATE_MIN_BLOCKS
+#define VEGAS_ITERATE_BOUNDS __launch_bounds__(256, VEGAS_ITERATE_MIN_BLOCKS)
+#else
+#define VEGAS_ITERATE_BOUNDS __launch_bounds__(256)
 #endif
 #ifndef VEGAS_SAMPLE_UNROLL
 #define VEGAS_SAMPLE_UNROLL 1
@@ -296,22 +298,20 @@ __device__ __forceinline__ void stage_grid(const double* __restrict__ edges, int
             shist[idx] = typename P::Hist(0);
 }
 
-// The samples [first, end) with step `stride` of iteration `it`: Philox words,
-// grid map, integrand, per-thread sums and the shared histogram.
-template <typename R, int D, int FN, bool ADAPT>
+// The samples [first, end) with step `stride` of iteration `it`: Philox words
+// (the first two rounds shared by a sample's calls), grid map, and the
+// integrand F in its staged coordinate; each sample's weight f J, the
+// integrand state and the bins go to sink(fw, f, bins).
+template <typename R, int D, typename F, typename Sink>
 __device__ __forceinline__ void sample_loop(unsigned long long first, unsigned long long end,
                                             unsigned long long stride, unsigned it,
                                             uint32_t c2base, const unsigned (&rk0)[10],
                                             const unsigned (&rk1)[10], const FnConsts& fc,
-                                            int N, int logr, R jstart, R n4, R nlast,
-                                            const typename Prec<R>::Pair* sgrid,
-                                            typename Prec<R>::Hist* shist, Acc<R>& acc,
-                                            unsigned& bad) {
+                                            int N, R jstart, R n4, R nlast,
+                                            const typename Prec<R>::Pair* sgrid, Sink& sink) {
     using P = Prec<R>;
     using Pair = typename P::Pair;
-    using H = typename P::Hist;
     constexpr int DC = (D + 3) / 4;  // Philox calls per sample
-    const int lane_copy = threadIdx.x & ((1 << logr) - 1);
     // per-call constants of the shared first two Philox rounds, for the
     // current high word of the sample index
     const uint32_t t_key = it ^ rk1[0];
@@ -332,10 +332,10 @@ __device__ __forceinline__ void sample_loop(unsigned long long first, unsigned l
         const uint32_t w2r0 = __umulhi(kPhiloxM0, i_lo) ^ t_key;
         const uint32_t hi1 = __umulhi(kPhiloxM1, w2r0);
         const uint32_t lo1 = kPhiloxM1 * w2r0;
-        Integrand<R, FN> f;
+        F f;
         f.begin();
         R J = jstart;
-        int hb[D];
+        uint32_t bins[D];
 #pragma unroll
         for (int q = 0; q < DC; ++q) {
             uint32_t w0 = hi1 ^ pc[q].a, w1 = lo1, w2 = lo0 ^ pc[q].b, w3 = pc[q].c;
@@ -351,24 +351,42 @@ __device__ __forceinline__ void sample_loop(unsigned long long first, unsigned l
                     const R x = P::fma(P::unit(l), g.y, g.x);
                     J *= g.y;
                     f.add(k, x, fc);
-                    if (ADAPT) hb[k] = ((k * N + (int)j) << logr) | lane_copy;
+                    if (Sink::kNeedBins) bins[k] = j;
                 }
             }
             if (sizeof(R) == 4) J *= (4 * q + 4 <= D) ? n4 : nlast;
         }
-        const R fw = f.value(fc) * J;
-        if (P::finite(fw)) {
+        sink(f.value(fc) * J, f, bins);
+    }
+}
+
+// The iterate kernels' sink: per-thread sums of f J and (f J)^2, the count of
+// non-finite weights, and (ADAPT) the shared histogram.
+template <typename R, int D, bool ADAPT>
+struct IterateSink {
+    static constexpr bool kNeedBins = ADAPT;
+    using H = typename Prec<R>::Hist;
+    Acc<R> acc;
+    unsigned bad = 0;
+    H* shist;
+    int N, logr, lane_copy;
+    __device__ __forceinline__ IterateSink(H* h, int n, int lr)
+        : shist(h), N(n), logr(lr), lane_copy(threadIdx.x & ((1 << lr) - 1)) {}
+    template <typename F>
+    __device__ __forceinline__ void operator()(R fw, const F&, const uint32_t (&bins)[D]) {
+        if (Prec<R>::finite(fw)) {
             acc.add(fw);
             if (ADAPT) {
                 const R fw2 = fw * fw;
 #pragma unroll
-                for (int k = 0; k < D; ++k) atomicAdd(&shist[hb[k]], (H)fw2);
+                for (int k = 0; k < D; ++k)
+                    atomicAdd(&shist[((k * N + (int)bins[k]) << logr) | lane_copy], (H)fw2);
             }
         } else {
             ++bad;
         }
     }
-}
+};
 
 // Add the block's histogram (its copies summed in double, times scale) into the
 // global one: one atomic per non-empty bin.
@@ -397,8 +415,7 @@ __device__ __forceinline__ void jacobian_factors(int N, R& n4, R& nlast) {
 // accumulate the refinement histogram.
 // ------------------------------------------------------------------------
 template <typename R, int D, int FN, bool ADAPT>
-__global__ void __launch_bounds__(256, VEGAS_ITERATE_MIN_BLOCKS)
-    vegas_iterate_kernel(const IterArgs a) {
+__global__ void VEGAS_ITERATE_BOUNDS vegas_iterate_kernel(const IterArgs a) {
     using P = Prec<R>;
     using Pair = typename P::Pair;
     using H = typename P::Hist;
@@ -437,12 +454,13 @@ __global__ void __launch_bounds__(256, VEGAS_ITERATE_MIN_BLOCKS)
     jacobian_factors<R, D>(N, n4, nlast);
     __syncthreads();
 
-    Acc<R> acc;
-    unsigned bad = 0;
-    sample_loop<R, D, FN, ADAPT>(
+    IterateSink<R, D, ADAPT> sink(shist, N, logr);
+    sample_loop<R, D, Integrand<R, FN>>(
         a.i0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x, a.i0 + a.n_chunk,
         (unsigned long long)gridDim.x * blockDim.x, it, a.integral_id << 8, a.rk0, a.rk1, a.fc,
-        N, logr, (R)j0, n4, nlast, sgrid, shist, acc, bad);
+        N, (R)j0, n4, nlast, sgrid, sink);
+    const Acc<R>& acc = sink.acc;
+    const unsigned bad = sink.bad;
 
     // Block reduction of the sums (fixed order), scaled back by 2^h / 2^2h.
     const double sc1 = ldexp(1.0, h), sc2 = ldexp(1.0, 2 * h);

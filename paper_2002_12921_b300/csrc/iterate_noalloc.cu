@@ -82,13 +82,14 @@ __global__ void __launch_bounds__(256) noalloc_iterate_kernel(const NoAllocArgs 
     jacobian_factors<R, D>(N, n4, nlast);
     __syncthreads();
 
-    Acc<R> acc;
-    unsigned bad = 0;
-    sample_loop<R, D, FN, ADAPT>((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x, a.n,
-                                 (unsigned long long)gridDim.x * blockDim.x, a.iter, 0u, a.rk0,
-                                 a.rk1, a.fc, N, logr,
-                                 (R)(sizeof(R) == 4 ? a.fc.C32 : a.fc.C), n4, nlast, sgrid,
-                                 shist, acc, bad);
+    IterateSink<R, D, ADAPT> sink(shist, N, logr);
+    sample_loop<R, D, Integrand<R, FN>>((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x,
+                                        a.n, (unsigned long long)gridDim.x * blockDim.x, a.iter,
+                                        0u, a.rk0, a.rk1, a.fc, N,
+                                        (R)(sizeof(R) == 4 ? a.fc.C32 : a.fc.C), n4, nlast, sgrid,
+                                        sink);
+    const Acc<R>& acc = sink.acc;
+    const unsigned bad = sink.bad;
 
     const double b1 = block_sum(acc.sum1(), sred);
     const double b2 = block_sum(acc.sum2(), sred);

@@ -148,24 +148,6 @@ int make_consts(int integrand, int dim, int nbins, const double* params, int npa
 
 using namespace vegas;
 
-struct vegas_state {
-    int dim, nbins, mode, integrand, max_iters;
-    uint64_t seed;
-    cudaStream_t stream;
-    int device;
-    int sm_count;
-    unsigned char* ws;
-    size_t ws_bytes;
-    double* edges;
-    double* hist;
-    double* log;
-    double* partials;
-    unsigned* ctrl;
-    int host_iters;  // iterations enqueued through this descriptor
-    vegas_config cfg;
-    FnConsts fc;
-    uint32_t rk0[10], rk1[10];
-};
 
 namespace {
 

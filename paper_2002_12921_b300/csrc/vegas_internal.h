@@ -84,3 +84,24 @@ cudaError_t launch_init(double* edges, double* hist, double* log, unsigned* ctrl
                         int nbins, int max_iters, cudaStream_t stream);
 
 }  // namespace vegas
+
+// The host descriptor behind the opaque vegas_state handle.
+struct vegas_state {
+    int dim, nbins, mode, integrand, max_iters;
+    uint64_t seed;
+    cudaStream_t stream;
+    int device;
+    int sm_count;
+    unsigned char* ws;
+    size_t ws_bytes;
+    double* edges;
+    double* hist;
+    double* log;
+    double* partials;
+    unsigned* ctrl;
+    int host_iters;  // iterations enqueued through this descriptor
+    vegas_config cfg;
+    vegas::FnConsts fc;
+    uint32_t rk0[10], rk1[10];
+};
+
