@@ -186,6 +186,42 @@ def time_mode(V, mode, steps, warmup, seed0, ws, flush, stream):
     return ms, fixed_ms, res
 
 
+def adjoint_timing(V, stream, reps=3):
+    """The differentiable d=8 workload (centres mu_i ~ U(0.3, 0.7) from PCG64(3),
+    a = 0.15): a grid adapted by 5 iterations of 1e6, then forward (I) and
+    backward (I and its 9 derivatives) over 1e8 samples regenerated from their
+    counters, per precision.  Returns ms per pass and the result."""
+    import torch
+
+    from paper_2002_12921_b300 import workloads as W
+
+    p = W.gauss_params(8, 0.15, W.c3_centres(3, 8))
+    n = 100_000_000
+    res = {}
+    for name, mode in (("fp32", V.VEGAS_FP32_EVAL), ("fp64", V.VEGAS_FP64)):
+        v = V.Vegas(8, 50, 3, mode, V.VEGAS_GAUSS, p, max_iters=8, stream=stream)
+        v.run([(1_000_000, 1)] * 5)
+        times = {}
+        for grad in (False, True):
+            v.gauss_adjoint(p, 5, n, grad)  # warm-up
+            ev = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                out = v.gauss_adjoint(p, 5, n, grad)
+                e1.record(stream)
+                ev.append((e0, e1))
+            torch.cuda.synchronize()
+            times["backward" if grad else "forward"] = statistics.median(
+                a.elapsed_time(b) for a, b in ev)
+        o = out.cpu().numpy()
+        v.close()
+        res[name] = {"forward_ms": times["forward"], "backward_ms": times["backward"],
+                     "samples": n, "I": float(o[0]), "dI_dmu": [float(x) for x in o[1:9]],
+                     "dI_da": float(o[9]), "sigma_dI_da": float(o[19] ** 0.5)}
+    return res
+
+
 def e2e_mode(V, mode, steps, seed0, ws, stream):
     """Same workload through the public API with host buffers: per step the
     starting grid and the integrand parameters come from pinned host memory and
@@ -330,6 +366,8 @@ def main():
         roofline["frac_at_measured_clock"] = achieved / (SMS * LANES_PER_SM * clk["sm_mhz"] * 1e6
                                                          / 1e12)
 
+    adjoint = adjoint_timing(V, stream) if rank == 0 else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline()
@@ -357,6 +395,7 @@ def main():
                            "ms_per_step": sum(ms64) / args.fp64_steps,
                            "kernel_ms_fixed_iteration": statistics.mean(fixed64)},
             "speedup_fp32_over_fp64": value / value64,
+            "adjoint_d8_a0.15_1e8": adjoint,
             "result": {"fp32": {"mean": m32, "sigma": s32, "pull": (m32 - EXACT) / s32},
                        "fp64": {"mean": m64, "sigma": s64, "pull": (m64 - EXACT) / s64},
                        "exact": EXACT, "sigma_ratio_fp32_fp64": s32 / s64,

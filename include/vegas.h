@@ -187,6 +187,54 @@ int vegas_sample_words(uint64_t seed, uint32_t integral_id, uint32_t iter, uint6
 int vegas_gauss_adjoint(vegas_state *s, const double *params, int nparams, uint32_t iter,
                         uint64_t n_samples, int grad, double *d_out);
 
+/* ---- many integrals in one persistent launch ------------------------------ */
+/* A batch holds `count` independent Eq. 1 Gaussian integrals (VegasFlow
+ * Sec. 3.1) of their own dimension (1..16) and samples per iteration, all with
+ * nbins bins per dimension, sharing one seed and one iteration schedule.
+ * Integral b draws its samples with integral_id = b in the counter (see the
+ * top of this file), so its result equals that of a single vegas_state run
+ * with the same grid, seed and iteration indices and integral id b.
+ * vegas_batch_iterate enqueues one iteration of every integral as one
+ * persistent launch -- thread blocks take (integral, sample range) tiles from
+ * an atomic ticket, without waiting on each other -- followed by one launch
+ * that refines every (integral, dimension) grid row and records each
+ * integral's estimate.  Those launches take no host synchronisation, so a
+ * whole schedule can be captured in a CUDA graph (vegas_batch_reset first,
+ * then the iterations) and replayed.  The caller owns the device workspace
+ * and the stream; the library copies the tile table and the per-integral
+ * constants into the workspace at vegas_batch_init (and at
+ * vegas_batch_set_config) with host-to-device copies ordered on the stream. */
+typedef struct vegas_batch vegas_batch;
+
+/* params: for integral b, [a_b, mu_b,1 .. mu_b,dims[b]], concatenated in
+ * order (sum_b (1 + dims[b]) doubles).  tile_samples 0 = default (65536). */
+int vegas_batch_workspace_bytes(int count, const int *dims, const uint64_t *n_samples,
+                                int nbins, int max_iters, size_t *bytes);
+int vegas_batch_init(vegas_batch **out, int count, const int *dims, const uint64_t *n_samples,
+                     int nbins, uint64_t seed, int mode, const double *params, int max_iters,
+                     void *d_workspace, size_t ws_bytes, void *cuda_stream);
+/* Block size (32..256, multiple of 32) and samples per tile (>= 4096, multiple
+ * of 32); 0 keeps the current value.  Rebuilds the tile table. */
+int vegas_batch_set_config(vegas_batch *b, int block_threads, uint64_t tile_samples);
+/* Order the batch's work on another stream (for graph capture on a side stream). */
+int vegas_batch_set_stream(vegas_batch *b, void *cuda_stream);
+/* Uniform grids, cleared histograms and logs, iteration counter 0 (device work
+ * on the stream; no host synchronisation). */
+int vegas_batch_reset(vegas_batch *b);
+/* One iteration of every integral (adapt != 0: histograms and refinement with
+ * damping alpha).  Asynchronous; VEGAS_ESTATE when max_iters is reached. */
+int vegas_batch_iterate(vegas_batch *b, int adapt, double alpha);
+/* Combined result of integral `index` over iterations first_iter .. done-1, as
+ * vegas_result.  Synchronises the stream. */
+int vegas_batch_result(vegas_batch *b, int index, int first_iter, double *mean, double *sigma,
+                       double *chi2_dof, int *n_iter);
+/* Log rows {S1, S2, n, nonfinite, I, var} of every integral: count x max_iters
+ * x 6 doubles (rows past the iterations done are zero).  Synchronises. */
+int vegas_batch_get_log(vegas_batch *b, double *host_rows);
+/* Grid of integral `index`: dims[index] x (nbins+1) doubles.  Synchronises. */
+int vegas_batch_get_grid(vegas_batch *b, int index, double *host_edges);
+int vegas_batch_destroy(vegas_batch *b);
+
 /* ---- entry point for callers that cannot allocate device memory ---------- */
 /* The paper has no counterpart to this call; it exists for callers that are not
  * allowed to allocate device memory -- code that runs inside a host framework

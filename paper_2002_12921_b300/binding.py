@@ -23,7 +23,11 @@ LOG_COLUMNS = ("S1", "S2", "n", "nonfinite", "I", "var")
 EXPORTED = ("vegas_workspace_bytes", "vegas_init_grid", "vegas_set_config", "vegas_iterate",
             "vegas_refine", "vegas_result", "vegas_get_iterations", "vegas_get_grid",
             "vegas_set_grid", "vegas_get_histogram", "vegas_sample_words", "vegas_destroy",
-            "vegas_strerror", "vegas_iterate_noalloc", "vegas_gauss_adjoint")
+            "vegas_strerror", "vegas_iterate_noalloc", "vegas_gauss_adjoint",
+            "vegas_batch_workspace_bytes", "vegas_batch_init", "vegas_batch_set_config",
+            "vegas_batch_set_stream", "vegas_batch_reset", "vegas_batch_iterate",
+            "vegas_batch_result", "vegas_batch_get_log", "vegas_batch_get_grid",
+            "vegas_batch_destroy")
 
 
 class VegasError(RuntimeError):
@@ -68,6 +72,17 @@ def lib():
         L.vegas_iterate_noalloc.argtypes = [vp, i32, i32, u64, ctypes.c_uint32, i32, vp, i32, u64,
                                              i32, dbl, vp, vp]
         L.vegas_gauss_adjoint.argtypes = [vp, vp, i32, ctypes.c_uint32, u64, i32, vp]
+        L.vegas_batch_workspace_bytes.argtypes = [i32, vp, vp, i32, i32, ctypes.POINTER(sz)]
+        L.vegas_batch_init.argtypes = [ctypes.POINTER(vp), i32, vp, vp, i32, u64, i32, vp, i32,
+                                       vp, sz, vp]
+        L.vegas_batch_set_config.argtypes = [vp, i32, u64]
+        L.vegas_batch_set_stream.argtypes = [vp, vp]
+        L.vegas_batch_reset.argtypes = [vp]
+        L.vegas_batch_iterate.argtypes = [vp, i32, dbl]
+        L.vegas_batch_result.argtypes = [vp, i32, i32, dp, dp, dp, ip]
+        L.vegas_batch_get_log.argtypes = [vp, vp]
+        L.vegas_batch_get_grid.argtypes = [vp, i32, vp]
+        L.vegas_batch_destroy.argtypes = [vp]
         L.vegas_destroy.argtypes = [vp]
         L.vegas_strerror.argtypes = [i32]
         L.vegas_strerror.restype = ctypes.c_char_p
@@ -254,3 +269,151 @@ class Vegas:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- batches
+def _batch_arrays(dims, n_samples, params_list):
+    dims_a = np.ascontiguousarray(dims, dtype=np.int32)
+    n_a = np.ascontiguousarray(n_samples, dtype=np.uint64)
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.float64)
+                                                for p in params_list]))
+    return dims_a, n_a, flat
+
+
+def vegas_batch_workspace_bytes(dims, n_samples, nbins, max_iters):
+    dims_a, n_a, _ = _batch_arrays(dims, n_samples, [[0.0]])
+    out = ctypes.c_size_t(0)
+    _check(lib().vegas_batch_workspace_bytes(len(dims_a), dims_a.ctypes.data, n_a.ctypes.data,
+                                             nbins, max_iters, ctypes.byref(out)),
+           "vegas_batch_workspace_bytes")
+    return out.value
+
+
+def vegas_batch_init(dims, n_samples, nbins, seed, mode, params_list, max_iters, d_workspace,
+                     ws_bytes, cuda_stream):
+    dims_a, n_a, flat = _batch_arrays(dims, n_samples, params_list)
+    h = ctypes.c_void_p(None)
+    _check(lib().vegas_batch_init(ctypes.byref(h), len(dims_a), dims_a.ctypes.data,
+                                  n_a.ctypes.data, nbins, seed & (2**64 - 1), mode,
+                                  flat.ctypes.data, max_iters, d_workspace, ws_bytes,
+                                  cuda_stream), "vegas_batch_init")
+    return h.value
+
+
+class VegasBatch:
+    """Many Eq. 1 Gaussian integrals advanced together (one persistent launch
+    per iteration); torch owns the workspace and supplies the stream."""
+
+    def __init__(self, dims, n_samples, nbins, seed, mode, params_list, max_iters=16,
+                 device="cuda", stream=None):
+        import torch
+
+        self.dims = [int(d) for d in dims]
+        self.nbins, self.max_iters = nbins, max_iters
+        self.ws_bytes = vegas_batch_workspace_bytes(self.dims, n_samples, nbins, max_iters)
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(
+            self.workspace.device)
+        self.handle = vegas_batch_init(self.dims, n_samples, nbins, seed, mode, params_list,
+                                       max_iters, self.workspace.data_ptr(), self.ws_bytes,
+                                       self.stream.cuda_stream)
+
+    def config(self, block_threads=0, tile_samples=0):
+        _check(lib().vegas_batch_set_config(self.handle, block_threads, tile_samples),
+               "vegas_batch_set_config")
+
+    def set_stream(self, stream):
+        self.stream = stream
+        _check(lib().vegas_batch_set_stream(self.handle, stream.cuda_stream),
+               "vegas_batch_set_stream")
+
+    def reset(self):
+        _check(lib().vegas_batch_reset(self.handle), "vegas_batch_reset")
+
+    def iterate(self, adapt=True, alpha=1.5):
+        _check(lib().vegas_batch_iterate(self.handle, 1 if adapt else 0, float(alpha)),
+               "vegas_batch_iterate")
+
+    def run(self, iters, adapt=True, alpha=1.5):
+        """Reset, then `iters` iterations (asynchronous)."""
+        self.reset()
+        for _ in range(iters):
+            self.iterate(adapt, alpha)
+
+    def capture(self, iters, adapt=True, alpha=1.5):
+        """A CUDA graph of reset + `iters` iterations, captured on a side stream;
+        replay() runs the whole schedule again."""
+        import torch
+
+        side = torch.cuda.Stream(device=self.workspace.device)
+        side.wait_stream(torch.cuda.current_stream(self.workspace.device))
+        old = self.stream
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            self.set_stream(side)
+            self.run(iters, adapt, alpha)  # warm-up outside the capture
+            side.synchronize()
+            with torch.cuda.graph(graph, stream=side):
+                self.run(iters, adapt, alpha)
+        torch.cuda.current_stream(self.workspace.device).wait_stream(side)
+        self.set_stream(old)
+        return graph
+
+    def result(self, index, first_iter=0):
+        m, s, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int()
+        rc = lib().vegas_batch_result(self.handle, index, first_iter, ctypes.byref(m),
+                                      ctypes.byref(s), ctypes.byref(c), ctypes.byref(n))
+        if rc not in (VEGAS_OK, VEGAS_ENONFINITE):
+            raise VegasError(rc, "vegas_batch_result")
+        return m.value, s.value, c.value, n.value, rc == VEGAS_ENONFINITE
+
+    def log(self):
+        out = np.zeros((len(self.dims), self.max_iters, 6))
+        _check(lib().vegas_batch_get_log(self.handle, out.ctypes.data), "vegas_batch_get_log")
+        return out
+
+    def grid(self, index):
+        e = np.empty((self.dims[index], self.nbins + 1))
+        _check(lib().vegas_batch_get_grid(self.handle, index, e.ctypes.data),
+               "vegas_batch_get_grid")
+        return e
+
+    def close(self):
+        if self.handle:
+            _check(lib().vegas_batch_destroy(self.handle), "vegas_batch_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune_batch(batch, blocks=(128, 256), tiles=(16384, 32768, 65536, 131072), reps=2,
+                   alpha=1.5):
+    """Pick (block_threads, tile_samples) for a batch by timing one adapting
+    iteration of every integral per candidate (CUDA events on the batch's
+    stream, best of `reps`).  Leaves the batch configured with the winner and
+    reset; returns (best, {candidate: ms})."""
+    import torch
+
+    timings = {}
+    for bt in blocks:
+        for ts in tiles:
+            batch.config(block_threads=bt, tile_samples=ts)
+            best = float("inf")
+            for _ in range(reps):
+                batch.reset()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(batch.stream)
+                batch.iterate(True, alpha)
+                e1.record(batch.stream)
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            timings[(bt, ts)] = best
+    choice = min(timings, key=timings.get)
+    batch.config(block_threads=choice[0], tile_samples=choice[1])
+    batch.reset()
+    return choice, timings

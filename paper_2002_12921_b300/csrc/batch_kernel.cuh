@@ -1,0 +1,118 @@
+// Many Vegas integrals in one persistent launch (the batch API of vegas.h).
+//
+// Work queue: the host cuts every integral's samples of an iteration into
+// tiles (integral b, first sample, count).  Each thread block repeatedly takes
+// the next tile index from an atomic ticket -- there is no waiting on other
+// blocks -- stages that integral's grid in shared memory, runs the shared
+// sample loop (integral_id = b in the Philox counter) and adds the tile's
+// sums and histogram to integral b's accumulators with FP64 atomics.  A
+// second, small launch refines every (integral, dimension) row and records
+// each integral's estimate (batch.cu).
+#pragma once
+
+#include "iterate_kernel.cuh"
+#include "vegas_internal.h"
+
+namespace vegas {
+
+struct BatchTile {
+    unsigned b;                // integral
+    unsigned count;            // samples in the tile
+    unsigned long long start;  // first sample index
+};
+
+struct BatchInfo {
+    int dim;
+    int pad;
+    unsigned long long n;         // samples per iteration
+    unsigned long long edge_off;  // offset of the grid rows in `edges`
+    unsigned long long hist_off;  // offset of the histogram rows in `hist`
+};
+
+struct BatchArgs {
+    const BatchTile* tiles;
+    const BatchInfo* info;
+    const FnConsts* consts;  // per integral (Eq. 1 staging and prefactors)
+    double* edges;
+    double* hist;
+    double* acc;             // per integral: S1, S2, nonfinite, unused
+    unsigned* ctrl;          // ticket
+    unsigned num_tiles;
+    unsigned iter;
+    int nbins;
+    int max_dim;
+    int hist_log2r;
+    unsigned rk0[10], rk1[10];
+};
+
+// One tile of integral b with compile-time dimension D.
+template <typename R, int D, bool ADAPT>
+__device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchTile& t,
+                                           typename Prec<R>::Pair* sgrid,
+                                           typename Prec<R>::Hist* shist, double* sred,
+                                           unsigned* sbad) {
+    const int N = a.nbins;
+    const int logr = ADAPT ? a.hist_log2r : 0;
+    const FnConsts& fc = a.consts[t.b];
+    const BatchInfo info = a.info[t.b];
+    stage_grid<R, D, ADAPT>(a.edges + info.edge_off, N, logr, fc, sgrid, shist);
+    R n4, nlast;
+    jacobian_factors<R, D>(N, n4, nlast);
+    __syncthreads();
+
+    IterateSink<R, D, ADAPT> sink(shist, N, logr);
+    sample_loop<R, D, Integrand<R, VEGAS_GAUSS>>(
+        t.start + threadIdx.x, t.start + t.count, blockDim.x, a.iter, t.b << 8, a.rk0, a.rk1,
+        fc, N, (R)(sizeof(R) == 4 ? fc.C32 : fc.C), n4, nlast, sgrid, sink);
+
+    const double s1 = block_sum(sink.acc.sum1(), sred);
+    const double s2 = block_sum(sink.acc.sum2(), sred);
+    const unsigned bad = block_sum(sink.bad, sbad);
+    if (ADAPT) {
+        __syncthreads();
+        flush_hist(shist, D * N, logr, 1.0, a.hist + info.hist_off);
+    }
+    if (threadIdx.x == 0) {
+        double* acc = a.acc + 4 * (size_t)t.b;
+        atomicAdd(acc + 0, s1);
+        atomicAdd(acc + 1, s2);
+        if (bad) atomicAdd(acc + 2, (double)bad);
+    }
+    __syncthreads();  // the next tile restages the shared memory
+}
+
+template <typename R, bool ADAPT>
+__global__ void __launch_bounds__(256) batch_iterate_kernel(const BatchArgs a) {
+    using P = Prec<R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double sred[32];
+    __shared__ unsigned sbad[32];
+    __shared__ unsigned s_tile;
+    typename P::Pair* sgrid = reinterpret_cast<typename P::Pair*>(smem_raw);
+    typename P::Hist* shist = reinterpret_cast<typename P::Hist*>(sgrid + a.max_dim * a.nbins);
+
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctrl[kTicket], 1u);
+        __syncthreads();
+        const unsigned ti = s_tile;
+        if (ti >= a.num_tiles) break;
+        const BatchTile t = a.tiles[ti];
+        switch (a.info[t.b].dim) {
+#define VEGAS_BATCH_CASE(D) \
+    case D: batch_tile<R, D, ADAPT>(a, t, sgrid, shist, sred, sbad); break;
+            VEGAS_BATCH_CASE(1) VEGAS_BATCH_CASE(2) VEGAS_BATCH_CASE(3) VEGAS_BATCH_CASE(4)
+            VEGAS_BATCH_CASE(5) VEGAS_BATCH_CASE(6) VEGAS_BATCH_CASE(7) VEGAS_BATCH_CASE(8)
+            VEGAS_BATCH_CASE(9) VEGAS_BATCH_CASE(10) VEGAS_BATCH_CASE(11) VEGAS_BATCH_CASE(12)
+            VEGAS_BATCH_CASE(13) VEGAS_BATCH_CASE(14) VEGAS_BATCH_CASE(15) VEGAS_BATCH_CASE(16)
+#undef VEGAS_BATCH_CASE
+            default: __syncthreads(); break;
+        }
+    }
+}
+
+// the batch iterate kernel of a precision, for the host (defined in
+// batch_f32.cu / batch_f64.cu)
+const void* batch_iterate_kernel_f32(bool adapt);
+const void* batch_iterate_kernel_f64(bool adapt);
+
+}  // namespace vegas

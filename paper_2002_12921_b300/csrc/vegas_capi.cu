@@ -144,6 +144,51 @@ int make_consts(int integrand, int dim, int nbins, const double* params, int npa
         return VEGAS_EINVAL;
     }
 }
+
+// Inverse-variance combination of log rows first .. n-1 (columns I = 4,
+// var = 5; rows `stride` doubles apart).  An iteration with zero variance makes
+// the result the plain mean with sigma 0.  NaNs when there is no row.
+void combine_rows(const double* rows, int stride, int first_iter, int n, double* mean,
+                  double* sigma, double* chi2_dof) {
+    const int K = n - first_iter;
+    double m = NAN, sg = NAN, c2 = NAN;
+    if (K > 0) {
+        bool zero = false;
+        for (int t = first_iter; t < n; ++t)
+            if (!(rows[(size_t)t * stride + 5] > 0.0)) zero = true;
+        if (zero) {
+            double acc = 0.0;
+            for (int t = first_iter; t < n; ++t) acc += rows[(size_t)t * stride + 4];
+            m = acc / K;
+            sg = 0.0;
+            double dev = 0.0;
+            for (int t = first_iter; t < n; ++t) {
+                const double d = rows[(size_t)t * stride + 4] - m;
+                dev += d * d;
+            }
+            c2 = K > 1 ? (dev == 0.0 ? 0.0 : INFINITY) : 0.0;
+        } else {
+            double w = 0.0, wi = 0.0;
+            for (int t = first_iter; t < n; ++t) {
+                const double I = rows[(size_t)t * stride + 4];
+                const double v = rows[(size_t)t * stride + 5];
+                w += 1.0 / v;
+                wi += I / v;
+            }
+            m = wi / w;
+            sg = std::sqrt(1.0 / w);
+            double chi = 0.0;
+            for (int t = first_iter; t < n; ++t) {
+                const double d = rows[(size_t)t * stride + 4] - m;
+                chi += d * d / rows[(size_t)t * stride + 5];
+            }
+            c2 = K > 1 ? chi / (K - 1) : 0.0;
+        }
+    }
+    *mean = m;
+    *sigma = sg;
+    *chi2_dof = c2;
+}
 }  // namespace vegas
 
 using namespace vegas;
@@ -409,42 +454,8 @@ int vegas_result(vegas_state* s, int first_iter, double* mean, double* sigma, do
     int rc = read_log(s, rows, s->max_iters, &n, &bad, first_iter);
     if (rc != VEGAS_OK) { delete[] rows; return rc; }
     if (n_iter) *n_iter = n;
-    const int K = n - first_iter;
     double m = NAN, sg = NAN, c2 = NAN;
-    if (K > 0) {
-        // inverse-variance weights; any zero-variance iteration: plain mean, sigma 0
-        bool zero = false;
-        for (int t = first_iter; t < n; ++t)
-            if (!(rows[(size_t)t * kLogStride + 5] > 0.0)) zero = true;
-        if (zero) {
-            double acc = 0.0;
-            for (int t = first_iter; t < n; ++t) acc += rows[(size_t)t * kLogStride + 4];
-            m = acc / K;
-            sg = 0.0;
-            double dev = 0.0;
-            for (int t = first_iter; t < n; ++t) {
-                const double d = rows[(size_t)t * kLogStride + 4] - m;
-                dev += d * d;
-            }
-            c2 = K > 1 ? (dev == 0.0 ? 0.0 : INFINITY) : 0.0;
-        } else {
-            double w = 0.0, wi = 0.0;
-            for (int t = first_iter; t < n; ++t) {
-                const double I = rows[(size_t)t * kLogStride + 4];
-                const double v = rows[(size_t)t * kLogStride + 5];
-                w += 1.0 / v;
-                wi += I / v;
-            }
-            m = wi / w;
-            sg = std::sqrt(1.0 / w);
-            double chi = 0.0;
-            for (int t = first_iter; t < n; ++t) {
-                const double d = rows[(size_t)t * kLogStride + 4] - m;
-                chi += d * d / rows[(size_t)t * kLogStride + 5];
-            }
-            c2 = K > 1 ? chi / (K - 1) : 0.0;
-        }
-    }
+    combine_rows(rows, kLogStride, first_iter, n, &m, &sg, &c2);
     delete[] rows;
     if (mean) *mean = m;
     if (sigma) *sigma = sg;

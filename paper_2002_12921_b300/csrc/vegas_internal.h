@@ -80,6 +80,8 @@ int hist_log2r(int mode, int dim, int nbins);
 size_t iterate_smem_bytes(int mode, int dim, int nbins, bool adapt, int log2r);
 
 cudaError_t launch_refine(const RefineArgs& a, cudaStream_t stream);
+void combine_rows(const double* rows, int stride, int first_iter, int n, double* mean,
+                  double* sigma, double* chi2_dof);
 cudaError_t launch_init(double* edges, double* hist, double* log, unsigned* ctrl, int dim,
                         int nbins, int max_iters, cudaStream_t stream);
 
