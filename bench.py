@@ -41,7 +41,7 @@ ALU_PEAK_TOPS = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
 
 # DRAM bytes per launch of the fixed-grid FP32 iterate kernel from the ncu
 # capture summarised in profiles/ (None until captured for this kernel build).
-ITERATE_TRAFFIC_BYTES = None
+ITERATE_TRAFFIC_BYTES = 60672  # dram read 60.7 KB + write 0 (this kernel build)
 
 
 def alg_ops_per_sample(d):
@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--legs", default="fp64,e2e,adjoint,batch,mix16",
+                    help="measurements besides the headline FP32 steps (comma list of "
+                         "fp64, e2e, adjoint, batch, mix16; '' for none)")
     return ap.parse_args()
 
 
@@ -427,16 +430,24 @@ def main():
         total_ms = float(t.item())
     value = SAMPLES_PER_STEP * args.steps * world / (total_ms / 1e3)
 
+    legs = {x for x in args.legs.split(",") if x}
     # plain FP64 on the same counters (equal error)
     # (its last step uses the same seed as the FP32 run's last step)
-    ms64, fixed64, res64 = time_mode(V, V.VEGAS_FP64, args.fp64_steps, 1,
-                                     seed0 + args.steps - args.fp64_steps, ws, flush, stream)
-    value64 = SAMPLES_PER_STEP * args.fp64_steps / (sum(ms64) / 1e3)
+    fp64 = None
+    if "fp64" in legs:
+        ms64, fixed64, res64 = time_mode(V, V.VEGAS_FP64, args.fp64_steps, 1,
+                                         seed0 + args.steps - args.fp64_steps, ws, flush, stream)
+        value64 = SAMPLES_PER_STEP * args.fp64_steps / (sum(ms64) / 1e3)
+        fp64 = {"value": value64, "unit": "samples/s", "ms_per_step": sum(ms64) / args.fp64_steps,
+                "kernel_ms_fixed_iteration": statistics.mean(fixed64)}
 
     # end to end through the public API with host buffers
-    e2e_t, h2d, d2h = e2e_mode(V, V.VEGAS_FP32_EVAL, max(3, min(args.steps, 5)), seed0, ws,
-                               stream)
-    e2e_value = SAMPLES_PER_STEP / statistics.median(e2e_t)
+    e2e = None
+    if "e2e" in legs:
+        e2e_t, h2d, d2h = e2e_mode(V, V.VEGAS_FP32_EVAL, max(3, min(args.steps, 5)), seed0, ws,
+                                   stream)
+        e2e = {"value": SAMPLES_PER_STEP / statistics.median(e2e_t), "unit": "samples/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     fixed_ms = statistics.mean(fixed32)
     ops = alg_ops_per_sample(DIM) * N_FIXED
@@ -451,9 +462,9 @@ def main():
         roofline["frac_at_measured_clock"] = achieved / (SMS * LANES_PER_SM * clk["sm_mhz"] * 1e6
                                                          / 1e12)
 
-    adjoint = adjoint_timing(V, stream) if rank == 0 else None
-    batch = batch_timing(V, stream) if rank == 0 else None
-    mix16 = mix16_timing(V, stream) if rank == 0 else None
+    adjoint = adjoint_timing(V, stream) if rank == 0 and "adjoint" in legs else None
+    batch = batch_timing(V, stream) if rank == 0 and "batch" in legs else None
+    mix16 = mix16_timing(V, stream) if rank == 0 and "mix16" in legs else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -462,7 +473,13 @@ def main():
 
     if rank == 0:
         m32, s32 = res32[0], res32[1]
-        m64, s64 = res64[0], res64[1]
+        result = {"fp32": {"mean": m32, "sigma": s32, "pull": (m32 - EXACT) / s32},
+                  "exact": EXACT}
+        if fp64:
+            m64, s64 = res64[0], res64[1]
+            result["fp64"] = {"mean": m64, "sigma": s64, "pull": (m64 - EXACT) / s64}
+            result["sigma_ratio_fp32_fp64"] = s32 / s64
+            result["abs_diff_fp32_fp64_in_sigma"] = abs(m32 - m64) / s64
         line = {
             "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup),
@@ -473,22 +490,16 @@ def main():
                        "l2": "256 MiB buffer written between timed steps, outside the step events",
                        "parallelism": f"{world} independent replicas"},
             "clocks": clk,
-            "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+            "e2e": e2e,
             "gpu_launches": LAUNCHES_PER_STEP * args.steps,
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "fp64_plain": {"value": value64, "unit": "samples/s",
-                           "ms_per_step": sum(ms64) / args.fp64_steps,
-                           "kernel_ms_fixed_iteration": statistics.mean(fixed64)},
-            "speedup_fp32_over_fp64": value / value64,
+            "fp64_plain": fp64,
+            "speedup_fp32_over_fp64": value / fp64["value"] if fp64 else None,
             "adjoint_d8_a0.15_1e8": adjoint,
             "batch_256_gauss_8iters": batch,
             "mix2_d16_N100_1e9_per_iter": mix16,
-            "result": {"fp32": {"mean": m32, "sigma": s32, "pull": (m32 - EXACT) / s32},
-                       "fp64": {"mean": m64, "sigma": s64, "pull": (m64 - EXACT) / s64},
-                       "exact": EXACT, "sigma_ratio_fp32_fp64": s32 / s64,
-                       "abs_diff_fp32_fp64_in_sigma": abs(m32 - m64) / s64},
+            "result": result,
         }
         print(json.dumps(line), flush=True)
     if dist:
