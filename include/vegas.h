@@ -169,6 +169,31 @@ int vegas_get_histogram(vegas_state *s, double *host_hist);
 int vegas_sample_words(uint64_t seed, uint32_t integral_id, uint32_t iter, uint64_t i0,
                        uint64_t n, int dim, uint32_t *d_out, void *cuda_stream);
 
+/* ---- one integral sharded over several devices ---------------------------- */
+/* Sample indices are global, so one iteration of n samples can be split into
+ * contiguous ranges computed on different devices (each with its own state,
+ * the same seed, grid and iteration count).  Per iteration, every rank:
+ *   vegas_iterate_range(s, n, begin, end, adapt)   its samples [begin, end);
+ *   vegas_shard_export(s, d_buf)                   packs its partial sums;
+ *   (sum the buffers over the ranks, e.g. an all-reduce)
+ *   vegas_shard_import(s, d_buf, n)                installs the totals;
+ *   vegas_refine(s, alpha)                         identical on every rank.
+ * The grids then stay identical across ranks and the log equals a single
+ * device's run up to the order of the sums.  The exchanged buffer holds
+ * 3 + dim*nbins doubles: {S1, S2, nonfinite, histogram (dim x nbins)}. */
+
+/* Samples [i_begin, i_end) of an iteration of n_total samples (0 <= i_begin <
+ * i_end <= n_total).  The log row holds this range's sums until
+ * vegas_shard_import replaces them.  Asynchronous. */
+int vegas_iterate_range(vegas_state *s, uint64_t n_total, uint64_t i_begin, uint64_t i_end,
+                        int adapt);
+/* Copy the last iteration's {S1, S2, nonfinite} and the histogram into d_buf
+ * (device, 3 + dim*nbins doubles).  Asynchronous. */
+int vegas_shard_export(vegas_state *s, double *d_buf);
+/* Replace the last iteration's sums and the histogram by d_buf's totals and
+ * recompute its I and var for n_total samples.  Asynchronous. */
+int vegas_shard_import(vegas_state *s, const double *d_buf, uint64_t n_total);
+
 /* Gradient of the Eq. 1 Gaussian integral with respect to its parameters, by
  * the reparameterised fixed-grid estimator: on the state's current (frozen)
  * grid, sample i of iteration `iter` is regenerated from its Philox counter

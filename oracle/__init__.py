@@ -38,6 +38,9 @@ def lib():
         L.oracle_iterate.argtypes = [i32, i32, vp, u64, u32, u32, u64, i32, vp, i32, i32,
                                      vp, vp, vp, vp]
         L.oracle_iterate.restype = i32
+        L.oracle_iterate_range.argtypes = [i32, i32, vp, u64, u32, u32, u64, u64, i32, vp, i32,
+                                           i32, vp, vp, vp, vp]
+        L.oracle_iterate_range.restype = i32
         L.oracle_estimate.argtypes = [dbl, dbl, u64, vp, vp]
         L.oracle_estimate.restype = None
         L.oracle_damp.argtypes = [dbl, dbl]
@@ -126,6 +129,22 @@ def iterate(edges, seed, it, n, fid, params, adapt, integral_id=0, nthreads=1):
         raise ValueError("oracle_iterate: invalid arguments")
     I, var = estimate(S1[0], S2[0], n)
     return dict(S1=float(S1[0]), S2=float(S2[0]), nonfinite=int(bad[0]), hist=hist, I=I, var=var)
+
+
+def iterate_range(edges, seed, it, first, count, fid, params, adapt, integral_id=0, nthreads=1):
+    """Partial sums of samples [first, first+count) of iteration it: dict(S1, S2,
+    nonfinite, hist (d x N) or None)."""
+    edges = _c(edges, np.float64)
+    dim, nb1 = edges.shape
+    p = _c(params if params is not None and len(params) else [0.0], np.float64)
+    hist = np.zeros((dim, nb1 - 1)) if adapt else None
+    S1, S2 = np.zeros(1), np.zeros(1)
+    bad = np.zeros(1, dtype=np.uint64)
+    if lib().oracle_iterate_range(dim, nb1 - 1, _ptr(edges), seed, integral_id, it, first, count,
+                                  fid, _ptr(p), 1 if adapt else 0, nthreads, _ptr(S1), _ptr(S2),
+                                  _ptr(hist), _ptr(bad)):
+        raise ValueError("oracle_iterate_range: invalid arguments")
+    return dict(S1=float(S1[0]), S2=float(S2[0]), nonfinite=int(bad[0]), hist=hist)
 
 
 def estimate(S1, S2, n):

@@ -259,15 +259,17 @@ static void *run_slice(void *arg)
     return NULL;
 }
 
-/* One Vegas iteration over sample indices [0, n).  Outputs the sums S1, S2, the
+/* One Vegas iteration over sample indices [first, first + n) (the whole
+ * iteration when first = 0 and n is its sample count; a shard otherwise).  Outputs the sums S1, S2, the
  * count of non-finite f*J values (left out of the sums), and, when adapt != 0,
  * adds the histogram sum over samples of (fJ)^2 per (dimension, bin) into hist
  * (dim * nbins doubles, caller-initialised).  The index range is cut into
  * nthreads contiguous slices whose sums are added in slice order.
  * Returns 0, or -1 on invalid arguments. */
-int oracle_iterate(int dim, int nbins, const double *edges, uint64_t seed, uint32_t integral_id,
-                   uint32_t iter, uint64_t n, int integrand, const double *params, int adapt,
-                   int nthreads, double *S1, double *S2, double *hist, uint64_t *nonfinite)
+int oracle_iterate_range(int dim, int nbins, const double *edges, uint64_t seed,
+                         uint32_t integral_id, uint32_t iter, uint64_t first, uint64_t n,
+                         int integrand, const double *params, int adapt, int nthreads,
+                         double *S1, double *S2, double *hist, uint64_t *nonfinite)
 {
     if (dim < 1 || dim > ORACLE_MAX_DIM || nbins < 1 || nthreads < 1) return -1;
     if (nthreads > 256) nthreads = 256;
@@ -282,8 +284,8 @@ int oracle_iterate(int dim, int nbins, const double *edges, uint64_t seed, uint3
         jb->edges = edges; jb->params = params; jb->seed = seed;
         jb->integral_id = integral_id; jb->iter = iter;
         /* slice t is [floor(n t / T), floor(n (t+1) / T)) */
-        jb->begin = (uint64_t)(((unsigned __int128)n * (uint64_t)t) / (uint64_t)nthreads);
-        jb->end = (uint64_t)(((unsigned __int128)n * (uint64_t)(t + 1)) / (uint64_t)nthreads);
+        jb->begin = first + (uint64_t)(((unsigned __int128)n * (uint64_t)t) / (uint64_t)nthreads);
+        jb->end = first + (uint64_t)(((unsigned __int128)n * (uint64_t)(t + 1)) / (uint64_t)nthreads);
         jb->hist = adapt ? calloc((size_t)dim * nbins, sizeof(long double)) : NULL;
     }
     if (nthreads == 1) {
@@ -313,6 +315,14 @@ int oracle_iterate(int dim, int nbins, const double *edges, uint64_t seed, uint3
     free(jobs);
     free(tids);
     return 0;
+}
+
+int oracle_iterate(int dim, int nbins, const double *edges, uint64_t seed, uint32_t integral_id,
+                   uint32_t iter, uint64_t n, int integrand, const double *params, int adapt,
+                   int nthreads, double *S1, double *S2, double *hist, uint64_t *nonfinite)
+{
+    return oracle_iterate_range(dim, nbins, edges, seed, integral_id, iter, 0, n, integrand,
+                                params, adapt, nthreads, S1, S2, hist, nonfinite);
 }
 
 /* Estimate of one iteration from its sums: I = S1/n and the unbiased variance

@@ -27,7 +27,8 @@ EXPORTED = ("vegas_workspace_bytes", "vegas_init_grid", "vegas_set_config", "veg
             "vegas_batch_workspace_bytes", "vegas_batch_init", "vegas_batch_set_config",
             "vegas_batch_set_stream", "vegas_batch_reset", "vegas_batch_iterate",
             "vegas_batch_result", "vegas_batch_get_log", "vegas_batch_get_grid",
-            "vegas_batch_destroy")
+            "vegas_batch_destroy", "vegas_iterate_range", "vegas_shard_export",
+            "vegas_shard_import")
 
 
 class VegasError(RuntimeError):
@@ -83,6 +84,9 @@ def lib():
         L.vegas_batch_get_log.argtypes = [vp, vp]
         L.vegas_batch_get_grid.argtypes = [vp, i32, vp]
         L.vegas_batch_destroy.argtypes = [vp]
+        L.vegas_iterate_range.argtypes = [vp, u64, u64, u64, i32]
+        L.vegas_shard_export.argtypes = [vp, vp]
+        L.vegas_shard_import.argtypes = [vp, vp, u64]
         L.vegas_destroy.argtypes = [vp]
         L.vegas_strerror.argtypes = [i32]
         L.vegas_strerror.restype = ctypes.c_char_p

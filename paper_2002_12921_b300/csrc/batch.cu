@@ -197,12 +197,13 @@ int build_tiles(vegas_batch* b) {
 
 int launch_batch_init(vegas_batch* b) {
     const BatchLayout& L = b->L;
-    batch_init_kernel<<<64, 256, 0, b->stream>>>(
-        at<double>(b, L.edges), L.n_edges, at<double>(b, L.hist), L.n_hist,
-        at<double>(b, L.acc), (size_t)b->count * 4, at<double>(b, L.log),
-        (size_t)b->count * b->max_iters * kLogStride, at<unsigned>(b, L.ctrl), b->nbins);
+    const cudaError_t e = launch_kernel(
+        batch_init_kernel, dim3(64), dim3(256), 0, b->stream, at<double>(b, L.edges), L.n_edges,
+        at<double>(b, L.hist), L.n_hist, at<double>(b, L.acc), (size_t)b->count * 4,
+        at<double>(b, L.log), (size_t)b->count * b->max_iters * kLogStride,
+        at<unsigned>(b, L.ctrl), b->nbins);
     b->iters = 0;
-    return cudaGetLastError() == cudaSuccess ? VEGAS_OK : VEGAS_ECUDA;
+    return e == cudaSuccess ? VEGAS_OK : VEGAS_ECUDA;
 }
 
 }  // namespace
@@ -388,9 +389,10 @@ int vegas_batch_iterate(vegas_batch* b, int adapt, double alpha) {
     pa.iter = (unsigned)b->iters;
     pa.adapt = ad ? 1 : 0;
     pa.alpha = alpha;
-    batch_post_kernel<<<(unsigned)L.n_rows, kPostThreads, (size_t)(4 * b->nbins + 2) *
-                        sizeof(double), b->stream>>>(pa);
-    if (cudaGetLastError() != cudaSuccess) return VEGAS_ECUDA;
+    if (launch_kernel(batch_post_kernel, dim3((unsigned)L.n_rows), dim3(kPostThreads),
+                      (size_t)(4 * b->nbins + 2) * sizeof(double), b->stream, pa) !=
+        cudaSuccess)
+        return VEGAS_ECUDA;
     b->iters++;
     return VEGAS_OK;
 }

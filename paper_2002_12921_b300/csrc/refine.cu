@@ -46,19 +46,37 @@ __global__ void init_kernel(double* edges, double* hist, double* log, unsigned* 
     for (int i = tid; i < kCtrlWords; i += nth) ctrl[i] = 0u;
 }
 
+// A log row from summed shard totals: S1, S2, n, nonfinite, I, var.
+__global__ void shard_row_kernel(double* row, const double* totals, unsigned long long n_total) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double n = (double)n_total;
+    const double S1 = totals[0], S2 = totals[1];
+    const double I = S1 / n;
+    const double var = (S2 / n - I * I) / (n - 1.0);
+    row[0] = S1;
+    row[1] = S2;
+    row[2] = n;
+    row[3] = totals[2];
+    row[4] = I;
+    row[5] = var > 0.0 ? var : 0.0;
+}
+
 }  // namespace
+
+cudaError_t launch_shard_row(double* row, const double* totals, unsigned long long n_total,
+                             cudaStream_t stream) {
+    return launch_kernel(shard_row_kernel, dim3(1), dim3(32), 0, stream, row, totals, n_total);
+}
 
 cudaError_t launch_refine(const RefineArgs& a, cudaStream_t stream) {
     const size_t smem = (size_t)(4 * a.nbins + 2) * sizeof(double);
-    refine_kernel<<<a.dim, kRefineThreads, smem, stream>>>(a);
-    return cudaGetLastError();
+    return launch_kernel(refine_kernel, dim3(a.dim), dim3(kRefineThreads), smem, stream, a);
 }
 
 cudaError_t launch_init(double* edges, double* hist, double* log, unsigned* ctrl, int dim,
                         int nbins, int max_iters, cudaStream_t stream) {
-    init_kernel<<<32, 256, 0, stream>>>(edges, hist, log, ctrl, dim, nbins,
-                                       max_iters * kLogStride);
-    return cudaGetLastError();
+    return launch_kernel(init_kernel, dim3(32), dim3(256), 0, stream, edges, hist, log, ctrl, dim,
+                         nbins, max_iters * kLogStride);
 }
 
 }  // namespace vegas

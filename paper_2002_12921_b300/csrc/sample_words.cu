@@ -52,6 +52,8 @@ extern "C" int vegas_sample_words(uint64_t seed, uint32_t integral_id, uint32_t 
     philox_round_keys(seed, a.rk0, a.rk1);
     unsigned long long blocks = (n + 255) / 256;
     if (blocks > 4096) blocks = 4096;
-    sample_words_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(a);
-    return cudaGetLastError() == cudaSuccess ? VEGAS_OK : VEGAS_ECUDA;
+    return launch_kernel(sample_words_kernel, dim3((unsigned)blocks), dim3(256), 0,
+                         static_cast<cudaStream_t>(cuda_stream), a) == cudaSuccess
+               ? VEGAS_OK
+               : VEGAS_ECUDA;
 }

@@ -337,8 +337,10 @@ int vegas_set_config(vegas_state* s, const vegas_config* cfg) {
     return VEGAS_OK;
 }
 
-int vegas_iterate(vegas_state* s, uint64_t n_samples, int adapt) {
-    if (!s || n_samples < 2) return VEGAS_EINVAL;
+// One iteration over the sample indices [begin, end): chunked launches of the
+// iterate kernel; the log row gets this range's sums, n = end - begin.
+static int enqueue_iteration(vegas_state* s, uint64_t begin, uint64_t end, int adapt) {
+    const uint64_t n_samples = end - begin;
     if (s->host_iters >= s->max_iters) return VEGAS_ESTATE;
     DeviceGuard g(s->device);
     if (!g.ok) return VEGAS_ECUDA;
@@ -386,12 +388,12 @@ int vegas_iterate(vegas_state* s, uint64_t n_samples, int adapt) {
     std::memcpy(a.rk1, s->rk1, sizeof(a.rk1));
     a.fc = s->fc;
 
-    for (uint64_t i0 = 0; i0 < n_samples; i0 += chunk) {
-        const uint64_t nc = (n_samples - i0) < chunk ? (n_samples - i0) : chunk;
+    for (uint64_t i0 = begin; i0 < end; i0 += chunk) {
+        const uint64_t nc = (end - i0) < chunk ? (end - i0) : chunk;
         a.i0 = i0;
         a.n_chunk = nc;
-        a.first_chunk = i0 == 0;
-        a.last_chunk = i0 + nc == n_samples;
+        a.first_chunk = i0 == begin;
+        a.last_chunk = i0 + nc == end;
         const uint64_t per_block = (uint64_t)block * s->cfg.min_samples_per_thread;
         long long grid = (long long)((nc + per_block - 1) / per_block);
         if (grid > grid_max) grid = grid_max;
@@ -403,6 +405,46 @@ int vegas_iterate(vegas_state* s, uint64_t n_samples, int adapt) {
     }
     s->host_iters++;
     return VEGAS_OK;
+}
+
+int vegas_iterate(vegas_state* s, uint64_t n_samples, int adapt) {
+    if (!s || n_samples < 2) return VEGAS_EINVAL;
+    return enqueue_iteration(s, 0, n_samples, adapt);
+}
+
+int vegas_iterate_range(vegas_state* s, uint64_t n_total, uint64_t i_begin, uint64_t i_end,
+                        int adapt) {
+    if (!s || n_total < 2 || i_begin >= i_end || i_end > n_total) return VEGAS_EINVAL;
+    return enqueue_iteration(s, i_begin, i_end, adapt);
+}
+
+int vegas_shard_export(vegas_state* s, double* d_buf) {
+    if (!s || !d_buf) return VEGAS_EINVAL;
+    if (s->host_iters < 1) return VEGAS_ESTATE;
+    DeviceGuard g(s->device);
+    if (!g.ok) return VEGAS_ECUDA;
+    const double* row = s->log + (size_t)(s->host_iters - 1) * kLogStride;
+    // {S1, S2} then nonfinite (row columns 0, 1, 3), then the histogram
+    if (cudaMemcpyAsync(d_buf, row, 2 * sizeof(double), cudaMemcpyDeviceToDevice, s->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(d_buf + 2, row + 3, sizeof(double), cudaMemcpyDeviceToDevice,
+                        s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(d_buf + 3, s->hist, (size_t)s->dim * s->nbins * sizeof(double),
+                        cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
+        return VEGAS_ECUDA;
+    return VEGAS_OK;
+}
+
+int vegas_shard_import(vegas_state* s, const double* d_buf, uint64_t n_total) {
+    if (!s || !d_buf || n_total < 2) return VEGAS_EINVAL;
+    if (s->host_iters < 1) return VEGAS_ESTATE;
+    DeviceGuard g(s->device);
+    if (!g.ok) return VEGAS_ECUDA;
+    if (cudaMemcpyAsync(s->hist, d_buf + 3, (size_t)s->dim * s->nbins * sizeof(double),
+                        cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
+        return VEGAS_ECUDA;
+    return cuda_status(launch_shard_row(s->log + (size_t)(s->host_iters - 1) * kLogStride, d_buf,
+                                        n_total, s->stream));
 }
 
 int vegas_refine(vegas_state* s, double alpha) {

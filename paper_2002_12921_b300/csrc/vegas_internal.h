@@ -5,9 +5,27 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <tuple>
+#include <utility>
+
 #include "../../include/vegas.h"
 
 namespace vegas {
+
+// Launch through cudaLaunchKernel and return its status: the launch's own
+// error, never a stale one left in the runtime's last-error state by an
+// unrelated earlier call.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                          cudaStream_t stream, Args&&... args) {
+    std::tuple<KArgs...> values(std::forward<Args>(args)...);
+    return std::apply(
+        [&](auto&... v) {
+            void* ptrs[] = {(void*)&v..., nullptr};
+            return cudaLaunchKernel((const void*)kernel, grid, block, ptrs, smem, stream);
+        },
+        values);
+}
 
 constexpr int kMaxDim = VEGAS_MAX_DIM;
 constexpr int kMaxBins = VEGAS_MAX_BINS;
@@ -82,6 +100,10 @@ size_t iterate_smem_bytes(int mode, int dim, int nbins, bool adapt, int log2r);
 cudaError_t launch_refine(const RefineArgs& a, cudaStream_t stream);
 void combine_rows(const double* rows, int stride, int first_iter, int n, double* mean,
                   double* sigma, double* chi2_dof);
+// Install summed shard totals {S1, S2, nonfinite} into a log row with I, var
+// for n_total samples.
+cudaError_t launch_shard_row(double* row, const double* totals, unsigned long long n_total,
+                             cudaStream_t stream);
 cudaError_t launch_init(double* edges, double* hist, double* log, unsigned* ctrl, int dim,
                         int nbins, int max_iters, cudaStream_t stream);
 

@@ -1,0 +1,142 @@
+"""One Vegas integral sharded over several devices.
+
+Sample indices are global and every sample is a pure function of its
+counter, so one iteration of n samples splits into contiguous index ranges
+that different devices (ranks) compute independently.  The only exchange is
+one sum per iteration of {S1, S2, nonfinite, histogram} (3 + d N doubles);
+after it every rank holds the totals and refines identically, so the grids
+never diverge and the result equals a single device's run up to the order of
+the sums.  (VegasFlow Sec. 3.3 distributes events over devices of one
+machine; this is that split, written for counter-based sampling.)
+
+An engine is what one rank computes with; it provides
+    iterate_range(n, begin, end, adapt), export() -> 1-d tensor,
+    import_(totals, n), refine(alpha), rows(), grid().
+``GpuShardEngine`` wraps a CUDA ``Vegas`` state (vegas_iterate_range /
+vegas_shard_export / vegas_shard_import); tests plug in CPU engines.
+"""
+import logging
+
+log = logging.getLogger(__name__)
+
+
+def shard_range(n, rank, world):
+    """Contiguous share [begin, end) of n sample indices for `rank` of `world`."""
+    return n * rank // world, n * (rank + 1) // world
+
+
+class GpuShardEngine:
+    """A rank's engine over a CUDA ``Vegas`` state."""
+
+    def __init__(self, vegas):
+        import torch
+
+        from . import binding as B
+
+        self.v, self.B = vegas, B
+        self.buf = torch.zeros(3 + vegas.dim * vegas.nbins, dtype=torch.float64,
+                               device=vegas.workspace.device)
+
+    def iterate_range(self, n, begin, end, adapt):
+        self.B._check(self.B.lib().vegas_iterate_range(self.v.handle, int(n), int(begin),
+                                                       int(end), 1 if adapt else 0),
+                      "vegas_iterate_range")
+
+    def export(self):
+        self.B._check(self.B.lib().vegas_shard_export(self.v.handle, self.buf.data_ptr()),
+                      "vegas_shard_export")
+        return self.buf
+
+    def import_(self, totals, n):
+        self.B._check(self.B.lib().vegas_shard_import(self.v.handle, totals.data_ptr(), int(n)),
+                      "vegas_shard_import")
+
+    def refine(self, alpha):
+        self.v.refine(alpha)
+
+    def rows(self):
+        return self.v.iterations()
+
+    def grid(self):
+        return self.v.grid()
+
+
+class ShardedVegas:
+    """Drives one engine per rank of a torch.distributed process group: each
+    iteration computes this rank's index range, all-reduces the partial sums
+    (NCCL for CUDA tensors, gloo for CPU ones) and refines.  Every iteration
+    needs n >= world size."""
+
+    def __init__(self, engine, group=None):
+        import torch.distributed as dist
+
+        self.engine, self.group, self.dist = engine, group, dist
+        self.rank = dist.get_rank(group) if dist.is_initialized() else 0
+        self.world = dist.get_world_size(group) if dist.is_initialized() else 1
+
+    def iterate(self, n, adapt, alpha=1.5):
+        if n < self.world:
+            raise ValueError("need at least one sample per rank")
+        begin, end = shard_range(n, self.rank, self.world)
+        self.engine.iterate_range(n, begin, end, adapt)
+        totals = self.engine.export()
+        if self.world > 1:
+            self.dist.all_reduce(totals, op=self.dist.ReduceOp.SUM, group=self.group)
+        self.engine.import_(totals, n)
+        if adapt:
+            self.engine.refine(alpha)
+
+    def run(self, schedule, alpha=1.5):
+        for n, adapt in schedule:
+            self.iterate(n, adapt, alpha)
+
+
+class RankFailure(RuntimeError):
+    """Raised (host side) by a rank that could not produce its share."""
+
+
+class VirtualRanks:
+    """`world` ranks emulated one after another in this process, each with its
+    own engine (on one GPU, or on the CPU), summing their exported partials on
+    the host side of the exchange.  A rank whose step raises RankFailure before
+    contributing is re-run: its counter range is deterministic, so the retry
+    reproduces exactly what the rank would have produced.  `fault` is an
+    optional hook fault(rank, iteration, attempt) that may raise RankFailure."""
+
+    def __init__(self, engines, fault=None, max_retries=2):
+        self.engines, self.fault, self.max_retries = list(engines), fault, max_retries
+        self.world = len(self.engines)
+        self.iteration = 0
+        self.failures = []
+
+    def _contribute(self, r, n, adapt):
+        begin, end = shard_range(n, r, self.world)
+        for attempt in range(self.max_retries + 1):
+            try:
+                if self.fault is not None:
+                    self.fault(r, self.iteration, attempt)
+                self.engines[r].iterate_range(n, begin, end, adapt)
+                return self.engines[r].export().clone()
+            except RankFailure as exc:
+                self.failures.append((self.iteration, r, attempt, str(exc)))
+                log.warning("rank %d failed at iteration %d (attempt %d): %s; re-running "
+                            "its range [%d, %d)", r, self.iteration, attempt, exc, begin, end)
+        raise RankFailure(f"rank {r} failed {self.max_retries + 1} times at iteration "
+                          f"{self.iteration}")
+
+    def iterate(self, n, adapt, alpha=1.5):
+        if n < self.world:
+            raise ValueError("need at least one sample per rank")
+        totals = None
+        for r in range(self.world):
+            part = self._contribute(r, n, adapt)
+            totals = part if totals is None else totals + part
+        for eng in self.engines:
+            eng.import_(totals, n)
+            if adapt:
+                eng.refine(alpha)
+        self.iteration += 1
+
+    def run(self, schedule, alpha=1.5):
+        for n, adapt in schedule:
+            self.iterate(n, adapt, alpha)

@@ -1,0 +1,84 @@
+"""CPU engines and process-group workers for the sharding tests (test
+infrastructure: the oracle computes each rank's share)."""
+import os
+import sys
+import traceback
+from datetime import timedelta
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+from paper_2002_12921_b300.shard import ShardedVegas  # noqa: E402
+
+
+class OracleEngine:
+    """One rank's engine computed by the FP64 oracle."""
+
+    def __init__(self, dim, nbins, seed, fid, params):
+        self.dim, self.nbins, self.seed, self.fid, self.params = dim, nbins, seed, fid, params
+        self.e = oracle.uniform_grid(dim, nbins)
+        self.it = 0
+        self.part = None
+        self.hist = np.zeros((dim, nbins))
+        self._rows = []
+
+    def iterate_range(self, n, begin, end, adapt):
+        self.part = oracle.iterate_range(self.e, self.seed, self.it, begin, end - begin, self.fid,
+                                         self.params, adapt)
+        if self.part["hist"] is None:
+            self.part["hist"] = np.zeros((self.dim, self.nbins))
+
+    def export(self):
+        p = self.part
+        return torch.tensor([p["S1"], p["S2"], float(p["nonfinite"])] + list(p["hist"].ravel()),
+                            dtype=torch.float64)
+
+    def import_(self, totals, n):
+        t = totals.numpy()
+        I, var = oracle.estimate(float(t[0]), float(t[1]), n)
+        self._rows.append([t[0], t[1], n, t[2], I, var])
+        self.hist = t[3:].reshape(self.dim, self.nbins).copy()
+        self.it += 1
+
+    def refine(self, alpha):
+        self.e = oracle.refine(self.e, self.hist, alpha)
+
+    def rows(self):
+        return np.array(self._rows)
+
+    def grid(self):
+        return self.e
+
+
+def gloo_worker(rank, world, port, out_dir, spec, fail_rank, fail_iter):
+    """One gloo rank: run the sharded schedule and save rows and grid; the rank
+    `fail_rank` raises (host side) before its share of iteration `fail_iter`;
+    the others record the error their next collective reports."""
+    import torch.distributed as dist
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world, timeout=timedelta(seconds=20))
+    eng = OracleEngine(*spec["engine"])
+    sv = ShardedVegas(eng)
+    try:
+        for t, (n, adapt) in enumerate(spec["schedule"]):
+            if rank == fail_rank and t == fail_iter:
+                raise RuntimeError("injected failure")
+            sv.iterate(n, adapt, spec["alpha"])
+        np.save(os.path.join(out_dir, f"rows{rank}.npy"), eng.rows())
+        np.save(os.path.join(out_dir, f"grid{rank}.npy"), eng.grid())
+    except Exception:
+        with open(os.path.join(out_dir, f"error{rank}.txt"), "w") as fh:
+            fh.write(traceback.format_exc())
+        if rank == fail_rank:
+            os._exit(3)  # the failing rank leaves without further collectives
+    finally:
+        try:
+            dist.destroy_process_group()
+        except Exception:
+            pass

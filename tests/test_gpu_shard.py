@@ -1,0 +1,64 @@
+"""Virtual ranks on one GPU: each rank is its own Vegas state computing its
+share of the counter range (vegas_iterate_range), the partial sums are added
+(vegas_shard_export / vegas_shard_import) and every rank refines; the result
+must equal one state's run and the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2002_12921_b300 as V
+from paper_2002_12921_b300 import workloads as W
+from paper_2002_12921_b300.shard import GpuShardEngine, RankFailure, VirtualRanks
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+P = W.gauss_params(6, 0.12, [0.3, 0.4, 0.5, 0.5, 0.6, 0.7])
+SCHED = [(300_000, 1), (300_000, 1), (200_001, 1), (500_000, 0)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    V.lib()
+
+
+def fp64_tol(edges):
+    return max(1e-12, 8 * edges.shape[0] * np.finfo(float).eps / np.min(np.diff(edges, axis=1)))
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_gpu_virtual_ranks_fp64_equal_oracle(world):
+    states = [V.Vegas(6, 40, 21, V.VEGAS_FP64, W.GAUSS, P, max_iters=8) for _ in range(world)]
+    VirtualRanks([GpuShardEngine(s) for s in states]).run(SCHED)
+    ref = oracle.run(6, 40, 21, W.GAUSS, P, SCHED, nthreads=8)
+    for s in states:
+        rows = s.iterations()
+        for t, r in enumerate(ref["log"]):
+            tol = 1e-12 if t == 0 else fp64_tol(ref["grids"][t])
+            assert rows[t][2] == SCHED[t][0]
+            assert abs(rows[t][4] - r["I"]) <= tol * abs(r["I"]), t
+        assert np.allclose(s.grid(), ref["edges"], rtol=1e-12, atol=1e-15)
+        s.close()
+
+
+def test_gpu_virtual_ranks_fp32_match_one_state_and_survive_a_failure():
+    def fault(rank, iteration, attempt):
+        if (rank, iteration, attempt) == (1, 1, 0):
+            raise RankFailure("injected")
+
+    one = V.Vegas(6, 40, 21, V.VEGAS_FP32_EVAL, W.GAUSS, P, max_iters=8)
+    one.run(SCHED)
+    ref = one.iterations()
+    states = [V.Vegas(6, 40, 21, V.VEGAS_FP32_EVAL, W.GAUSS, P, max_iters=8) for _ in range(2)]
+    vr = VirtualRanks([GpuShardEngine(s) for s in states], fault=fault)
+    vr.run(SCHED)
+    assert len(vr.failures) == 1
+    for s in states:
+        rows = s.iterations()
+        # float histograms summed per shard round differently: the FP32 bound
+        assert np.allclose(rows[:, 4], ref[:, 4], rtol=1e-5, atol=0)
+        assert np.allclose(s.grid(), one.grid(), rtol=0, atol=1e-6)
+        s.close()
+    one.close()
