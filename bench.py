@@ -10,8 +10,10 @@ FP64 path runs the same workload (same counters, hence equal error) and is
 reported beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun each rank runs its own replica (own seeds, no collective on the
-data path); rank 0 prints one JSON line.
+Under torchrun (N > 1) the headline integral is sharded over the ranks: every
+rank keeps the per-GPU sample counts (weak scaling), computes its range of
+sample indices and the partial sums are all-reduced once per iteration; the
+other legs run on each rank independently.  Rank 0 prints one JSON line.
 """
 import argparse
 import json
@@ -159,33 +161,69 @@ def run_step(V, ws, stream, mode, seed, fixed_events=None):
     return h
 
 
+def run_step_sharded(V, stream, mode, seed, world, fixed_events=None):
+    """One step of the same integral sharded over `world` ranks (weak scaling:
+    every rank keeps the per-GPU sample counts, so an iteration has `world`
+    times as many samples): each rank computes its counter range, the partial
+    sums and histogram are all-reduced (NCCL), every rank refines."""
+    import torch
+
+    from paper_2002_12921_b300 import workloads as W
+    from paper_2002_12921_b300.shard import GpuShardEngine, ShardedVegas
+
+    v = V.Vegas(DIM, NBINS, seed, mode, V.VEGAS_GAUSS, W.gauss_params(DIM, A),
+                max_iters=IT_ADAPT + IT_FIXED, stream=stream)
+    sv = ShardedVegas(GpuShardEngine(v))
+    for _ in range(IT_ADAPT):
+        sv.iterate(N_ADAPT * world, True, ALPHA)
+    for _ in range(IT_FIXED):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sv.iterate(N_FIXED * world, False)
+        e1.record(stream)
+        if fixed_events is not None:
+            fixed_events.append((e0, e1))
+    return v
+
+
 LAUNCHES_PER_STEP = 1 + IT_ADAPT * 2 + IT_FIXED  # init, iterate+refine, fixed iterate
 
 
-def time_mode(V, mode, steps, warmup, seed0, ws, flush, stream):
+def time_mode(V, mode, steps, warmup, seed0, ws, flush, stream, world=1):
     """Device time of `steps` whole steps (events on the library's stream);
-    step s uses seed seed0 + s, and the result returned is the last step's."""
+    step s uses seed seed0 + s, and the result returned is the last step's.
+    world > 1: the step is sharded over the ranks (run_step_sharded)."""
     import torch
+
+    def step(seed, fixed=None):
+        if world > 1:
+            return run_step_sharded(V, stream, mode, seed, world, fixed)
+        return run_step(V, ws, stream, mode, seed, fixed)
 
     handles = []
     for w in range(warmup):
-        handles.append(run_step(V, ws, stream, mode, seed0 + 1000 + w))
+        handles.append(step(seed0 + 1000 + w))
     torch.cuda.synchronize()
     step_events, fixed = [], []
     for s in range(steps):
         l2_flush(flush)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        handles.append(run_step(V, ws, stream, mode, seed0 + s, fixed))
+        handles.append(step(seed0 + s, fixed))
         e1.record(stream)
         step_events.append((e0, e1))
     torch.cuda.synchronize()
     ms = [a.elapsed_time(b) for a, b in step_events]
     fixed_ms = [a.elapsed_time(b) for a, b in fixed]
     last = handles[-1]
-    res = V.vegas_result(last, IT_ADAPT)
-    for h in handles:
-        V.vegas_destroy(h)
+    if world > 1:
+        res = last.result(IT_ADAPT)
+        for v in handles:
+            v.close()
+    else:
+        res = V.vegas_result(last, IT_ADAPT)
+        for h in handles:
+            V.vegas_destroy(h)
     return ms, fixed_ms, res
 
 
@@ -420,8 +458,10 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(torch.cuda.current_device())
+    # N > 1: one integral sharded over the ranks (same seed everywhere)
+    seed_main = 2 if world > 1 else seed0
     ms32, fixed32, res32 = time_mode(V, V.VEGAS_FP32_EVAL, args.steps, max(3, args.warmup),
-                                     seed0, ws, flush, stream)
+                                     seed_main, ws, flush, stream, world)
     clk = clocks.stop()
     total_ms = sum(ms32)
     if dist:
@@ -488,10 +528,14 @@ def main():
             "config": {"workload": WORKLOAD, "dim": DIM, "nbins": NBINS, "a": A, "alpha": ALPHA,
                        "samples_per_step": SAMPLES_PER_STEP, "mode": "fp32_eval_fp64_accumulate",
                        "l2": "256 MiB buffer written between timed steps, outside the step events",
-                       "parallelism": f"{world} independent replicas"},
+                       "parallelism": (f"one integral sharded over {world} ranks: counter "
+                                       "ranges, NCCL all-reduce of S1, S2 and the histogram "
+                                       "per iteration" if world > 1 else "1 GPU")},
             "clocks": clk,
             "e2e": e2e,
-            "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+            # sharded: one more kernel per iteration installs the reduced sums
+            "gpu_launches": (LAUNCHES_PER_STEP + (IT_ADAPT + IT_FIXED if world > 1 else 0))
+            * args.steps,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "fp64_plain": fp64,
