@@ -297,6 +297,21 @@ int vegas_iterate_noalloc(double *d_edges, int dim, int nbins, uint64_t seed, ui
                           int mode, const double *params, int nparams, uint64_t n_samples,
                           int adapt, double alpha, double *d_result, void *cuda_stream);
 
+/* ---- checkpoint / resume -------------------------------------------------- */
+/* A state's resumable content as a flat little-endian blob: shape, mode,
+ * integrand and its parameters, seed, iteration count, launch configuration,
+ * the grid, the histogram (an adapting iteration not yet refined) and the
+ * iteration log.  Because every sample is a function of (seed, iteration,
+ * index), a state imported from a blob continues exactly as the exported one
+ * would have.  Export synchronises the stream.  With buf == NULL, *bytes
+ * receives the blob size; otherwise *bytes must hold at least that size. */
+int vegas_export_state(vegas_state *s, void *buf, size_t *bytes);
+/* Create a state from a blob (VEGAS_EINVAL if it is malformed or of another
+ * format version) on a caller workspace of at least vegas_workspace_bytes()
+ * for the blob's shape and iteration capacity.  Asynchronous on the stream. */
+int vegas_import_state(vegas_state **out, const void *buf, size_t bytes, void *d_workspace,
+                       size_t ws_bytes, void *cuda_stream);
+
 /* Release the descriptor (not the caller's workspace).  Synchronises the
  * stream first.  NULL is accepted. */
 int vegas_destroy(vegas_state *s);

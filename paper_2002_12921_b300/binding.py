@@ -28,7 +28,7 @@ EXPORTED = ("vegas_workspace_bytes", "vegas_init_grid", "vegas_set_config", "veg
             "vegas_batch_set_stream", "vegas_batch_reset", "vegas_batch_iterate",
             "vegas_batch_result", "vegas_batch_get_log", "vegas_batch_get_grid",
             "vegas_batch_destroy", "vegas_iterate_range", "vegas_shard_export",
-            "vegas_shard_import")
+            "vegas_shard_import", "vegas_export_state", "vegas_import_state")
 
 
 class VegasError(RuntimeError):
@@ -87,6 +87,8 @@ def lib():
         L.vegas_iterate_range.argtypes = [vp, u64, u64, u64, i32]
         L.vegas_shard_export.argtypes = [vp, vp]
         L.vegas_shard_import.argtypes = [vp, vp, u64]
+        L.vegas_export_state.argtypes = [vp, vp, ctypes.POINTER(sz)]
+        L.vegas_import_state.argtypes = [ctypes.POINTER(vp), vp, sz, vp, sz, vp]
         L.vegas_destroy.argtypes = [vp]
         L.vegas_strerror.argtypes = [i32]
         L.vegas_strerror.restype = ctypes.c_char_p
@@ -200,6 +202,23 @@ def vegas_gauss_adjoint(h, params, it, n_samples, grad, d_out):
                                      1 if grad else 0, d_out), "vegas_gauss_adjoint")
 
 
+def vegas_export_state(h):
+    """The state's checkpoint blob (bytes)."""
+    n = ctypes.c_size_t(0)
+    _check(lib().vegas_export_state(h, None, ctypes.byref(n)), "vegas_export_state")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().vegas_export_state(h, buf, ctypes.byref(n)), "vegas_export_state")
+    return buf.raw[: n.value]
+
+
+def vegas_import_state(blob, d_workspace, ws_bytes, cuda_stream):
+    """A new state (handle) from a checkpoint blob."""
+    h = ctypes.c_void_p(None)
+    _check(lib().vegas_import_state(ctypes.byref(h), blob, len(blob), d_workspace, ws_bytes,
+                                    cuda_stream), "vegas_import_state")
+    return h.value
+
+
 def vegas_destroy(h):
     if h:
         _check(lib().vegas_destroy(h), "vegas_destroy")
@@ -223,6 +242,29 @@ class Vegas:
 
     def config(self, **kw):
         vegas_set_config(self.handle, **kw)
+
+    def export_state(self):
+        return vegas_export_state(self.handle)
+
+    @classmethod
+    def from_state(cls, blob, device="cuda", stream=None):
+        """Resume a state from vegas_export_state's blob (header words: dim at
+        offset 16, nbins at 24, max_iters at 48)."""
+        import struct
+
+        import torch
+
+        dim, nbins = struct.unpack_from("<QQ", blob, 16)
+        (max_iters,) = struct.unpack_from("<Q", blob, 48)
+        self = cls.__new__(cls)
+        self.dim, self.nbins = int(dim), int(nbins)
+        self.ws_bytes = vegas_workspace_bytes(self.dim, self.nbins, int(max_iters))
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(
+            self.workspace.device)
+        self.handle = vegas_import_state(blob, self.workspace.data_ptr(), self.ws_bytes,
+                                         self.stream.cuda_stream)
+        return self
 
     def iterate(self, n, adapt):
         vegas_iterate(self.handle, n, adapt)

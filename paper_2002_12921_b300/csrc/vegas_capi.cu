@@ -295,6 +295,9 @@ int vegas_init_grid(vegas_state** out, int dim, int nbins, uint64_t seed, int mo
     s->device = attr.device;
     int rc = make_consts(integrand, dim, nbins, params, nparams, &s->fc);
     if (rc != VEGAS_OK) { delete s; return rc; }
+    s->nparams = !params || nparams < 0 ? 0 : (nparams > 1 + 2 * kMaxDim ? 1 + 2 * kMaxDim
+                                                                           : nparams);
+    for (int i = 0; i < s->nparams; ++i) s->params[i] = params[i];
     philox_round_keys(seed, s->rk0, s->rk1);
     default_config(&s->cfg);
 

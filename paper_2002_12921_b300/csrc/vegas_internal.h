@@ -127,5 +127,7 @@ struct vegas_state {
     vegas_config cfg;
     vegas::FnConsts fc;
     uint32_t rk0[10], rk1[10];
+    double params[1 + 2 * VEGAS_MAX_DIM];  // the integrand parameters as given
+    int nparams;
 };
 

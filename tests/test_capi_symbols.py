@@ -65,3 +65,12 @@ def test_init_rejects_bad_arguments_before_touching_a_device(lib):
 def test_strerror_covers_codes(lib):
     texts = {V.vegas_strerror(c) for c in range(6)}
     assert len(texts) == 6 and V.vegas_strerror(99) == "unknown status"
+
+
+def test_import_rejects_malformed_blobs_without_a_device(lib):
+    h = ctypes.c_void_p()
+    bad = b"NOTVEGAS" + bytes(200)
+    assert lib.vegas_import_state(ctypes.byref(h), bad, len(bad), None, 0, None) == 1
+    short = b"VEGASB3\x00" + bytes(16)
+    assert lib.vegas_import_state(ctypes.byref(h), short, len(short), None, 0, None) == 1
+    assert h.value is None

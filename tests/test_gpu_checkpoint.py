@@ -1,0 +1,42 @@
+"""Checkpoint / resume: a state exported mid-run and imported into a fresh
+workspace continues exactly as the original (samples are functions of their
+counters)."""
+import numpy as np
+import pytest
+
+import paper_2002_12921_b300 as V
+from paper_2002_12921_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    V.lib()
+
+
+@pytest.mark.parametrize("mode", [V.VEGAS_FP64, V.VEGAS_FP32_EVAL])
+def test_resume_equals_uninterrupted_run(mode):
+    p = W.gauss_params(5, 0.12, [0.3, 0.45, 0.5, 0.55, 0.7])
+    a = V.Vegas(5, 30, 77, mode, W.GAUSS, p, max_iters=8)
+    a.config(chunk_samples=70_001)
+    a.run([(200_000, 1)] * 3)
+    a.iterate(150_000, 1)  # exported between an adapting iteration and its refinement
+    blob = a.export_state()
+    b = V.Vegas.from_state(blob)
+    for v in (a, b):
+        v.refine(1.5)
+        v.run([(180_000, 1), (300_000, 0)])
+    ra, rb = a.iterations(), b.iterations()
+    assert ra.shape == rb.shape == (6, 6)
+    tol = 1e-12 if mode == V.VEGAS_FP64 else 1e-5
+    assert np.allclose(rb[:, 4], ra[:, 4], rtol=tol, atol=0)
+    assert np.allclose(b.grid(), a.grid(), rtol=0, atol=1e-14 if mode == V.VEGAS_FP64 else 1e-6)
+    assert b.result(4)[3] == 6
+    # a blob of the resumed state describes the same run
+    assert len(b.export_state()) == len(a.export_state())
+    a.close()
+    b.close()
