@@ -398,10 +398,32 @@ def cpu_baseline(fast=False):
                    nthreads=cores)
     dt = time.perf_counter() - t0
     n = sum(s for s, _ in sched)
-    return {"value": n / dt, "unit": "samples/s", "cores": cores, "kind": "oracle",
-            "sample": f"{WORKLOAD}: " + " + ".join(f"{s:.0e}{'a' if a else 'f'}" for s, a in sched)
-            + f" = {n:.1e} samples, FP64, {cores} threads", "seconds": dt,
-            "result": r["mean"]}
+    out = {"value": n / dt, "unit": "samples/s", "cores": cores, "kind": "oracle",
+           "sample": f"{WORKLOAD}: " + " + ".join(f"{s:.0e}{'a' if a else 'f'}" for s, a in sched)
+           + f" = {n:.1e} samples, FP64, {cores} threads", "seconds": dt,
+           "result": r["mean"], "cpu_model": cpu_model()}
+    if not fast:
+        # the same oracle on one thread, on a smaller sample of the workload
+        sched1 = [(N_ADAPT // 10, 1), (N_ADAPT // 5, 0)]
+        t0 = time.perf_counter()
+        oracle.run(DIM, NBINS, 2, W.GAUSS, W.gauss_params(DIM, A), sched1, alpha=ALPHA,
+                   nthreads=1)
+        dt1 = time.perf_counter() - t0
+        n1 = sum(s for s, _ in sched1)
+        out["single_core"] = {"value": n1 / dt1, "unit": "samples/s",
+                              "sample": f"{n1:.1e} samples (1e6 adapting + 2e6 fixed), 1 thread"}
+    return out
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
 
 
 def reference_arm(args, rank, world):
@@ -509,7 +531,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline()
-        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu_model",
+                                  "single_core")}
 
     if rank == 0:
         m32, s32 = res32[0], res32[1]

@@ -81,6 +81,10 @@ extern "C" {
 #define VEGAS_FLAT 2
 #define VEGAS_GENZ_DISC 3
 #define VEGAS_GENZ_PPEAK 4
+/* VEGAS_USER       an integrand compiled by the caller (include/vegas_user_integrand.cuh),
+ *                  attached with vegas_set_user_integrand before the first
+ *                  iteration; params ignored. */
+#define VEGAS_USER 5
 
 /* ---- limits --------------------------------------------------------------- */
 #define VEGAS_MAX_DIM 16
@@ -311,6 +315,42 @@ int vegas_export_state(vegas_state *s, void *buf, size_t *bytes);
  * for the blob's shape and iteration capacity.  Asynchronous on the stream. */
 int vegas_import_state(vegas_state **out, const void *buf, size_t bytes, void *d_workspace,
                        size_t ws_bytes, void *cuda_stream);
+
+/* ---- user-supplied integrands (VegasFlow Sec. 2.3: integrands written in
+ * C++ or CUDA and linked into the integrator) ------------------------------- */
+/* The kernels of an integrand compiled in the caller's own CUDA translation
+ * unit by the VEGAS_USER_INTEGRAND macro of include/vegas_user_integrand.cuh,
+ * which returns a pointer to this descriptor.  The library never launches
+ * the caller's kernels itself: it sizes the launch with `prepare` and issues
+ * it through `launch`, both code of the caller's module (so the kernels need
+ * not be registered with the library's CUDA runtime).
+ *   dim         the dimension the kernels were compiled for
+ *   args_bytes  the size of the kernels' argument block, checked against the
+ *               library's own (a mismatch means the two were built from
+ *               different headers)
+ *   prepare     for (mode, adapt, block threads, dynamic shared bytes): raise
+ *               the kernel's shared-memory limit if needed and store its
+ *               resident blocks per SM in *blocks; returns a cudaError_t value
+ *   launch      enqueue the kernel of (mode, adapt) with the argument block
+ *               `args` on `stream`; returns a cudaError_t value */
+typedef struct {
+    int dim;
+    size_t args_bytes;
+    int (*prepare)(int mode, int adapt, int block, size_t smem, int *blocks);
+    int (*launch)(int mode, int adapt, const void *args, unsigned grid, unsigned block,
+                  size_t smem, void *stream);
+} vegas_user_integrand;
+
+/* Attach user kernels to a state created with integrand VEGAS_USER (the
+ * descriptor is copied; d_data is a device pointer, owned by the caller and
+ * kept alive while the state iterates, handed unchanged to every evaluation
+ * of the integrand; it may be NULL).  The state then iterates, refines,
+ * shards and checkpoints as with a built-in integrand; a state restored by
+ * vegas_import_state needs the call again.  VEGAS_EINVAL if the state is not
+ * VEGAS_USER, the dimension or the argument-block size differ, or a callback
+ * is NULL.  Iterating a VEGAS_USER state without it returns VEGAS_ESTATE. */
+int vegas_set_user_integrand(vegas_state *s, const vegas_user_integrand *u, const void *d_data);
+
 
 /* Release the descriptor (not the caller's workspace).  Synchronises the
  * stream first.  NULL is accepted. */

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libvegas_b300.so")
 
 VEGAS_OK, VEGAS_EINVAL, VEGAS_ECUDA, VEGAS_ENONFINITE, VEGAS_ESTATE, VEGAS_ENOSPACE = range(6)
 VEGAS_FP64, VEGAS_FP32_EVAL = 0, 1
-VEGAS_GAUSS, VEGAS_GAUSS_MIX2, VEGAS_FLAT, VEGAS_GENZ_DISC, VEGAS_GENZ_PPEAK = range(5)
+VEGAS_GAUSS, VEGAS_GAUSS_MIX2, VEGAS_FLAT, VEGAS_GENZ_DISC, VEGAS_GENZ_PPEAK, VEGAS_USER = range(6)
 VEGAS_MAX_DIM, VEGAS_MAX_BINS, VEGAS_MAX_DIM_X_BINS = 16, 1024, 8192
 VEGAS_NOALLOC_MAX_DIM_X_BINS, VEGAS_NOALLOC_MAX_BLOCKS = 4096, 2048
 LOG_COLUMNS = ("S1", "S2", "n", "nonfinite", "I", "var")
@@ -28,7 +28,8 @@ EXPORTED = ("vegas_workspace_bytes", "vegas_init_grid", "vegas_set_config", "veg
             "vegas_batch_set_stream", "vegas_batch_reset", "vegas_batch_iterate",
             "vegas_batch_result", "vegas_batch_get_log", "vegas_batch_get_grid",
             "vegas_batch_destroy", "vegas_iterate_range", "vegas_shard_export",
-            "vegas_shard_import", "vegas_export_state", "vegas_import_state")
+            "vegas_shard_import", "vegas_export_state", "vegas_import_state",
+            "vegas_set_user_integrand")
 
 
 class VegasError(RuntimeError):
@@ -89,6 +90,7 @@ def lib():
         L.vegas_shard_import.argtypes = [vp, vp, u64]
         L.vegas_export_state.argtypes = [vp, vp, ctypes.POINTER(sz)]
         L.vegas_import_state.argtypes = [ctypes.POINTER(vp), vp, sz, vp, sz, vp]
+        L.vegas_set_user_integrand.argtypes = [vp, vp, vp]
         L.vegas_destroy.argtypes = [vp]
         L.vegas_strerror.argtypes = [i32]
         L.vegas_strerror.restype = ctypes.c_char_p
@@ -219,6 +221,30 @@ def vegas_import_state(blob, d_workspace, ws_bytes, cuda_stream):
     return h.value
 
 
+class vegas_user_integrand(ctypes.Structure):
+    """The descriptor VEGAS_USER_INTEGRAND returns (include/vegas.h)."""
+    _fields_ = [("dim", ctypes.c_int), ("args_bytes", ctypes.c_size_t),
+                ("prepare", ctypes.c_void_p), ("launch", ctypes.c_void_p)]
+
+
+def load_user_integrand(so_path, name):
+    """Load a caller's integrand library (see build.build_user_integrand) and
+    return (its CDLL, the address of descriptor `name`); keep the CDLL alive
+    while a state uses the descriptor."""
+    mod = ctypes.CDLL(so_path)
+    fn = getattr(mod, name)
+    fn.restype = ctypes.c_void_p
+    fn.argtypes = []
+    desc = fn()
+    if not desc:
+        raise VegasError(VEGAS_EINVAL, name)
+    return mod, desc
+
+
+def vegas_set_user_integrand(h, desc, d_data=0):
+    _check(lib().vegas_set_user_integrand(h, desc, d_data or None), "vegas_set_user_integrand")
+
+
 def vegas_destroy(h):
     if h:
         _check(lib().vegas_destroy(h), "vegas_destroy")
@@ -242,6 +268,14 @@ class Vegas:
 
     def config(self, **kw):
         vegas_set_config(self.handle, **kw)
+
+    def set_user_integrand(self, desc, data=None, module=None):
+        """Attach a VEGAS_USER_INTEGRAND descriptor (an address, e.g. from
+        load_user_integrand) to a VEGAS_USER state; `data` is an optional
+        device tensor whose pointer the integrand receives (kept alive with
+        `module`, the integrand's library, as long as this state)."""
+        vegas_set_user_integrand(self.handle, desc, data.data_ptr() if data is not None else 0)
+        self._user_refs = (data, module)
 
     def export_state(self):
         return vegas_export_state(self.handle)

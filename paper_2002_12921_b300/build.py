@@ -4,6 +4,7 @@ Every translation unit under csrc/ is compiled by nvcc for
 ``-gencode arch=compute_103a,code=sm_103a`` (in parallel, one process per
 unit) and linked into ``paper_2002_12921_b300/_build/libvegas_b300.so``.
 Usage: ``python -m paper_2002_12921_b300.build [--force] [--verbose]``.
+``build_user_integrand`` compiles a caller's integrand file the same way.
 """
 import concurrent.futures as cf
 import glob
@@ -17,6 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "libvegas_b300.so"
 LIB = os.path.join(OUT_DIR, LIB_NAME)
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "--expt-relaxed-constexpr"]
@@ -36,7 +38,7 @@ def sources():
 def headers():
     return (sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) +
             sorted(glob.glob(os.path.join(CSRC, "*.h"))) +
-            [os.path.join(os.path.dirname(HERE), "include", "vegas.h")])
+            [os.path.join(INCLUDE, "vegas.h"), os.path.join(INCLUDE, "vegas_user_integrand.cuh")])
 
 
 def _stale(target, deps):
@@ -79,6 +81,25 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, LIB)
     return LIB
+
+
+def build_user_integrand(src: str, out: str, force: bool = False, verbose: bool = False) -> str:
+    """Compile a caller's integrand file (one that uses VEGAS_USER_INTEGRAND of
+    include/vegas_user_integrand.cuh) into the shared library `out`, with the
+    library's own architecture and flags, if it is missing or older than its
+    source or the library's headers.  Returns `out`."""
+    if force or _stale(out, [src] + headers()):
+        os.makedirs(os.path.dirname(os.path.abspath(out)), exist_ok=True)
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = [nvcc()] + ARCH + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + \
+            ["-I", INCLUDE, "-shared", src, "-o", tmp]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+        if verbose and r.stderr:
+            sys.stderr.write(f"== {os.path.basename(src)}\n{r.stderr}")
+        os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

@@ -174,6 +174,7 @@ const void* adjoint_kernel(int mode, int dim, bool grad) {
 extern "C" int vegas_gauss_adjoint(vegas_state* s, const double* params, int nparams,
                                    uint32_t iter, uint64_t n_samples, int grad,
                                    double* d_out) {
+    vegas::TraceRange trace_("vegas_gauss_adjoint");
     using namespace vegas;
     if (!s || !params || !d_out || nparams < 1 + s->dim) return VEGAS_EINVAL;
     if (n_samples < 2 || n_samples > (1ull << 40)) return VEGAS_EINVAL;

@@ -332,6 +332,7 @@ int vegas_batch_reset(vegas_batch* b) {
 }
 
 int vegas_batch_iterate(vegas_batch* b, int adapt, double alpha) {
+    vegas::TraceRange trace_("vegas_batch_iterate");
     if (!b) return VEGAS_EINVAL;
     if (adapt && !(alpha >= 0.0 && std::isfinite(alpha))) return VEGAS_EINVAL;
     if (b->iters >= b->max_iters) return VEGAS_ESTATE;

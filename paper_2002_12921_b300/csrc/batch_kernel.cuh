@@ -65,8 +65,8 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchTile& 
         t.start + threadIdx.x, t.start + t.count, blockDim.x, a.iter, t.b << 8, a.rk0, a.rk1,
         fc, N, (R)(sizeof(R) == 4 ? fc.C32 : fc.C), n4, nlast, sgrid, sink);
 
-    const double s1 = block_sum(sink.acc.sum1(), sred);
-    const double s2 = block_sum(sink.acc.sum2(), sred);
+    const double s1 = sink.acc.block1(reinterpret_cast<FloatFloat*>(sred));
+    const double s2 = sink.acc.block2(reinterpret_cast<FloatFloat*>(sred));
     const unsigned bad = block_sum(sink.bad, sbad);
     if (ADAPT) {
         __syncthreads();

@@ -239,6 +239,44 @@ __device__ __forceinline__ T block_sum(T v, T* sbuf) {
     return v;
 }
 
+// A float-float value h + l (|l| <= ulp(h) / 2) and its sum: TwoSum of the
+// high parts (exact), then the low parts, then renormalisation.  About 48
+// significant bits, in FP32 instructions only.
+struct FloatFloat {
+    float h, l;
+};
+
+__device__ __forceinline__ FloatFloat ff_add(FloatFloat a, FloatFloat b) {
+    const float s = a.h + b.h;
+    const float v = s - a.h;
+    const float e = (a.h - (s - v)) + (b.h - v);  // s + e == a.h + b.h exactly
+    const float t = e + (a.l + b.l);
+    const float h = s + t;
+    return {h, t - (h - s)};
+}
+
+// Sum of per-thread float-float values over the block in a fixed order
+// (shuffle tree, then warp 0), converted to double once, in thread 0: the
+// float path's block reduction keeps FP64 instructions off every warp.
+__device__ __forceinline__ double block_sum_ff(FloatFloat v, FloatFloat* sbuf) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = ff_add(v, {__shfl_down_sync(0xffffffffu, v.h, o), __shfl_down_sync(0xffffffffu, v.l, o)});
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sbuf[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    if (wid == 0) {
+        v = lane < nw ? sbuf[lane] : FloatFloat{0.f, 0.f};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            v = ff_add(v, {__shfl_down_sync(0xffffffffu, v.h, o),
+                           __shfl_down_sync(0xffffffffu, v.l, o)});
+    }
+    return (double)v.h + (double)v.l;
+}
+
 // Per-thread accumulators: compensated in float, plain in double.
 template <typename R>
 struct Acc;
@@ -260,6 +298,13 @@ struct Acc<float> {
     }
     __device__ __forceinline__ double sum1() const { return (double)s1 - (double)c1; }
     __device__ __forceinline__ double sum2() const { return (double)s2 - (double)c2; }
+    // the block totals of sum1 / sum2 (valid in thread 0)
+    __device__ __forceinline__ double block1(FloatFloat* sbuf) const {
+        return block_sum_ff(ff_add({s1, 0.f}, {-c1, 0.f}), sbuf);
+    }
+    __device__ __forceinline__ double block2(FloatFloat* sbuf) const {
+        return block_sum_ff(ff_add({s2, 0.f}, {-c2, 0.f}), sbuf);
+    }
 };
 
 template <>
@@ -271,6 +316,12 @@ struct Acc<double> {
     }
     __device__ __forceinline__ double sum1() const { return s1; }
     __device__ __forceinline__ double sum2() const { return s2; }
+    __device__ __forceinline__ double block1(FloatFloat* sbuf) const {
+        return block_sum(s1, reinterpret_cast<double*>(sbuf));
+    }
+    __device__ __forceinline__ double block2(FloatFloat* sbuf) const {
+        return block_sum(s2, reinterpret_cast<double*>(sbuf));
+    }
 };
 
 // ------------------------------------------------------------------------
@@ -388,16 +439,21 @@ struct IterateSink {
     }
 };
 
-// Add the block's histogram (its copies summed in double, times scale) into the
-// global one: one atomic per non-empty bin.
+// Add the block's histogram (its copies summed, times scale) into the global
+// one: one atomic per non-empty bin.  A thread sums one bin's R copies in the
+// histogram's own type, starting at copy (bin mod R) so that the lanes of a
+// warp read distinct banks; only the bin's total passes through double (on
+// this GPU an FP64 warp instruction occupies the FP64 pipe ~60 cycles, so the
+// flush keeps them to one conversion and one multiply per 32 bins).
 template <typename H>
 __device__ __forceinline__ void flush_hist(const H* shist, int nbins_total, int logr,
                                            double scale, double* hist) {
-    const int R = 1 << logr;
-    for (int idx = threadIdx.x; idx < nbins_total; idx += blockDim.x) {
-        double v = 0.0;
-        for (int c = 0; c < R; ++c) v += (double)shist[(idx << logr) + c];
-        if (v != 0.0) atomicAdd(&hist[idx], v * scale);
+    const int m = (1 << logr) - 1;
+    for (int b = threadIdx.x; b < nbins_total; b += blockDim.x) {
+        const H* row = shist + (b << logr);
+        H v = row[b & m];
+        for (int c = 1; c <= m; ++c) v += row[(b + c) & m];
+        if (v != (H)0) atomicAdd(&hist[b], (double)v * scale);
     }
 }
 
@@ -411,11 +467,11 @@ __device__ __forceinline__ void jacobian_factors(int N, R& n4, R& nlast) {
 }
 
 // ------------------------------------------------------------------------
-// The kernel.  R = float or double, D = dimension, FN = integrand id, ADAPT =
-// accumulate the refinement histogram.
+// The kernel body.  R = float or double, D = dimension, F = integrand type,
+// ADAPT = accumulate the refinement histogram.
 // ------------------------------------------------------------------------
-template <typename R, int D, int FN, bool ADAPT>
-__global__ void VEGAS_ITERATE_BOUNDS vegas_iterate_kernel(const IterArgs a) {
+template <typename R, int D, typename F, bool ADAPT>
+__device__ __forceinline__ void iterate_body(const IterArgs& a) {
     using P = Prec<R>;
     using Pair = typename P::Pair;
     using H = typename P::Hist;
@@ -455,7 +511,7 @@ __global__ void VEGAS_ITERATE_BOUNDS vegas_iterate_kernel(const IterArgs a) {
     __syncthreads();
 
     IterateSink<R, D, ADAPT> sink(shist, N, logr);
-    sample_loop<R, D, Integrand<R, FN>>(
+    sample_loop<R, D, F>(
         a.i0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x, a.i0 + a.n_chunk,
         (unsigned long long)gridDim.x * blockDim.x, it, a.integral_id << 8, a.rk0, a.rk1, a.fc,
         N, (R)j0, n4, nlast, sgrid, sink);
@@ -464,8 +520,8 @@ __global__ void VEGAS_ITERATE_BOUNDS vegas_iterate_kernel(const IterArgs a) {
 
     // Block reduction of the sums (fixed order), scaled back by 2^h / 2^2h.
     const double sc1 = ldexp(1.0, h), sc2 = ldexp(1.0, 2 * h);
-    const double b1 = block_sum(acc.sum1(), sred);
-    const double b2 = block_sum(acc.sum2(), sred);
+    const double b1 = acc.block1(reinterpret_cast<FloatFloat*>(sred));
+    const double b2 = acc.block2(reinterpret_cast<FloatFloat*>(sred));
     const unsigned bb = block_sum(bad, sbad);
     if (ADAPT) {
         __syncthreads();
@@ -516,6 +572,21 @@ __global__ void VEGAS_ITERATE_BOUNDS vegas_iterate_kernel(const IterArgs a) {
         }
         a.ctrl[kTicket] = 0u;
     }
+}
+
+// The built-in integrands' kernel.
+template <typename R, int D, int FN, bool ADAPT>
+__global__ void VEGAS_ITERATE_BOUNDS vegas_iterate_kernel(const IterArgs a) {
+    iterate_body<R, D, Integrand<R, FN>, ADAPT>(a);
+}
+
+// The same kernel for an integrand type F supplied by the caller's own
+// translation unit (include/vegas_user_integrand.cuh): F provides begin(),
+// add(k, x, fc) and value(fc) in the plain coordinate x (the state must use
+// VEGAS_USER, whose staging is the identity and whose prefactor is 1).
+template <typename R, int D, typename F, bool ADAPT>
+__global__ void VEGAS_ITERATE_BOUNDS vegas_user_iterate_kernel(const IterArgs a) {
+    iterate_body<R, D, F, ADAPT>(a);
 }
 
 }  // namespace vegas

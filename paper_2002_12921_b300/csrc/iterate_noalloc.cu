@@ -91,8 +91,8 @@ __global__ void __launch_bounds__(256) noalloc_iterate_kernel(const NoAllocArgs 
     const Acc<R>& acc = sink.acc;
     const unsigned bad = sink.bad;
 
-    const double b1 = block_sum(acc.sum1(), sred);
-    const double b2 = block_sum(acc.sum2(), sred);
+    const double b1 = acc.block1(reinterpret_cast<FloatFloat*>(sred));
+    const double b2 = acc.block2(reinterpret_cast<FloatFloat*>(sred));
     const unsigned bb = block_sum(bad, sbad);
     if (ADAPT) {
         __syncthreads();
@@ -172,6 +172,7 @@ extern "C" int vegas_iterate_noalloc(double* d_edges, int dim, int nbins, uint64
                                      uint32_t iter, int mode, const double* params, int nparams,
                                      uint64_t n_samples, int adapt, double alpha,
                                      double* d_result, void* cuda_stream) {
+    vegas::TraceRange trace_("vegas_iterate_noalloc");
     using namespace vegas;
     if (dim < 1 || dim > kMaxDim || nbins < 1 || nbins > kMaxBins) return VEGAS_EINVAL;
     if (dim * nbins > kNaMaxDimBins) return VEGAS_ENOSPACE;

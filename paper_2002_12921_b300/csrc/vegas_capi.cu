@@ -103,6 +103,7 @@ int make_consts(int integrand, int dim, int nbins, const double* params, int npa
         return VEGAS_OK;
     }
     case VEGAS_FLAT:
+    case VEGAS_USER:  // identity staging: the caller's integrand sees x itself
         fc->C = npow;
         fc->C32 = 1.0;
         return VEGAS_OK;
@@ -267,6 +268,7 @@ int vegas_workspace_bytes(int dim, int nbins, int max_iters, size_t* bytes) {
 int vegas_init_grid(vegas_state** out, int dim, int nbins, uint64_t seed, int mode, int integrand,
                     const double* params, int nparams, int max_iters, void* d_workspace,
                     size_t ws_bytes, void* cuda_stream) {
+    vegas::TraceRange trace_("vegas_init_grid");
     if (!out) return VEGAS_EINVAL;
     *out = nullptr;
     if (!shape_ok(dim, nbins, max_iters) || !d_workspace) return VEGAS_EINVAL;
@@ -343,27 +345,35 @@ int vegas_set_config(vegas_state* s, const vegas_config* cfg) {
 // One iteration over the sample indices [begin, end): chunked launches of the
 // iterate kernel; the log row gets this range's sums, n = end - begin.
 static int enqueue_iteration(vegas_state* s, uint64_t begin, uint64_t end, int adapt) {
+    vegas::TraceRange trace_("vegas_iterate");
     const uint64_t n_samples = end - begin;
     if (s->host_iters >= s->max_iters) return VEGAS_ESTATE;
     DeviceGuard g(s->device);
     if (!g.ok) return VEGAS_ECUDA;
 
     const bool ad = adapt != 0;
-    const void* kern = kernel_for(s, ad);
-    if (!kern) return VEGAS_EINVAL;
+    const bool user = s->integrand == VEGAS_USER;
+    if (user && !s->user.launch) return VEGAS_ESTATE;
+    const void* kern = user ? nullptr : kernel_for(s, ad);
+    if (!user && !kern) return VEGAS_EINVAL;
     const int log2r = ad ? hist_log2r(s->mode, s->dim, s->nbins) : 0;
     const size_t smem = iterate_smem_bytes(s->mode, s->dim, s->nbins, ad, log2r);
-    // static shared memory (~0.5 KB) counts against the 48 KB default as well
-    if (smem > 40 * 1024) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return VEGAS_ECUDA;
-    }
     const int block = s->cfg.block_threads;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) != cudaSuccess ||
-        occ < 1)
-        return VEGAS_ECUDA;
+    if (user) {
+        if (s->user.prepare(s->mode, ad ? 1 : 0, block, smem, &occ) != 0 || occ < 1)
+            return VEGAS_ECUDA;
+    } else {
+        // static shared memory (~0.5 KB) counts against the 48 KB default as well
+        if (smem > 40 * 1024 &&
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
+            return VEGAS_ECUDA;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) !=
+                cudaSuccess ||
+            occ < 1)
+            return VEGAS_ECUDA;
+    }
     const int bps = s->cfg.blocks_per_sm > 0 && s->cfg.blocks_per_sm < occ ? s->cfg.blocks_per_sm
                                                                            : occ;
     long long grid_max = (long long)s->sm_count * bps;
@@ -401,12 +411,27 @@ static int enqueue_iteration(vegas_state* s, uint64_t begin, uint64_t end, int a
         long long grid = (long long)((nc + per_block - 1) / per_block);
         if (grid > grid_max) grid = grid_max;
         if (grid < 1) grid = 1;
-        void* args[] = {&a};
-        const cudaError_t e =
-            cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(block), args, smem, s->stream);
-        if (e != cudaSuccess) return VEGAS_ECUDA;
+        if (user) {
+            if (s->user.launch(s->mode, ad ? 1 : 0, &a, (unsigned)grid, (unsigned)block, smem,
+                               s->stream) != 0)
+                return VEGAS_ECUDA;
+        } else {
+            void* args[] = {&a};
+            if (cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(block), args, smem, s->stream) !=
+                cudaSuccess)
+                return VEGAS_ECUDA;
+        }
     }
     s->host_iters++;
+    return VEGAS_OK;
+}
+
+int vegas_set_user_integrand(vegas_state* s, const vegas_user_integrand* u, const void* d_data) {
+    if (!s || !u || s->integrand != VEGAS_USER || u->dim != s->dim ||
+        u->args_bytes != sizeof(IterArgs) || !u->prepare || !u->launch)
+        return VEGAS_EINVAL;
+    s->user = *u;
+    s->fc.user = d_data;
     return VEGAS_OK;
 }
 
@@ -451,6 +476,7 @@ int vegas_shard_import(vegas_state* s, const double* d_buf, uint64_t n_total) {
 }
 
 int vegas_refine(vegas_state* s, double alpha) {
+    vegas::TraceRange trace_("vegas_refine");
     if (!s || !(alpha >= 0.0) || !std::isfinite(alpha)) return VEGAS_EINVAL;
     DeviceGuard g(s->device);
     if (!g.ok) return VEGAS_ECUDA;
@@ -490,6 +516,7 @@ static int read_log(vegas_state* s, double* rows, int max_rows, int* n_rows, int
 
 int vegas_result(vegas_state* s, int first_iter, double* mean, double* sigma, double* chi2_dof,
                  int* n_iter) {
+    vegas::TraceRange trace_("vegas_result");
     if (!s || first_iter < 0) return VEGAS_EINVAL;
     DeviceGuard g(s->device);
     if (!g.ok) return VEGAS_ECUDA;

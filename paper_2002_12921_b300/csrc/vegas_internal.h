@@ -5,12 +5,23 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <tuple>
 #include <utility>
 
 #include "../../include/vegas.h"
 
 namespace vegas {
+
+// A named range around a C-ABI call, visible in profilers' timelines (NVTX;
+// nearly free when no tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Launch through cudaLaunchKernel and return its status: the launch's own
 // error, never a stale one left in the runtime's last-error state by an
@@ -55,6 +66,7 @@ struct FnConsts {
     double t64[kMaxDim];    // GENZ_DISC: thresholds a_k
     float d32[kMaxDim];     // MIX2: z_B - z_A in the float coordinate; GENZ_DISC: c_k log2 e
     float t32[kMaxDim];     // GENZ_DISC: thresholds a_k
+    const void* user;       // VEGAS_USER: the caller's device data pointer
 };
 
 // Fill FnConsts for an integrand (VEGAS_EINVAL on bad parameters).
@@ -129,5 +141,6 @@ struct vegas_state {
     uint32_t rk0[10], rk1[10];
     double params[1 + 2 * VEGAS_MAX_DIM];  // the integrand parameters as given
     int nparams;
+    vegas_user_integrand user;  // VEGAS_USER: the caller's kernels (launch == NULL: unset)
 };
 

@@ -6,7 +6,7 @@ that different devices (ranks) compute independently.  The only exchange is
 one sum per iteration of {S1, S2, nonfinite, histogram} (3 + d N doubles);
 after it every rank holds the totals and refines identically, so the grids
 never diverge and the result equals a single device's run up to the order of
-the sums.  (VegasFlow Sec. 3.3 distributes events over devices of one
+the sums.  (VegasFlow Sec. 3.4 distributes events over devices of one
 machine; this is that split, written for counter-based sampling.)
 
 An engine is what one rank computes with; it provides

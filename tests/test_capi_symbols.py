@@ -74,3 +74,20 @@ def test_import_rejects_malformed_blobs_without_a_device(lib):
     short = b"VEGASB3\x00" + bytes(16)
     assert lib.vegas_import_state(ctypes.byref(h), short, len(short), None, 0, None) == 1
     assert h.value is None
+
+
+def test_user_integrand_descriptors_load_without_a_device(lib):
+    """A caller's integrand file compiles against include/vegas_user_integrand.cuh
+    and its descriptors carry the compiled dimension and callbacks; the
+    library rejects one without a state."""
+    so = build.build_user_integrand(os.path.join(ROOT, "tests", "user_integrands.cu"),
+                                    os.path.join(ROOT, "tests", "_build", "libuser_integrands.so"))
+    sizes = set()
+    for name, dim in [("user_gauss_d4", 4), ("user_gauss_d8", 8), ("user_sum_square_d5", 5),
+                      ("user_sine_d3", 3)]:
+        mod, addr = V.load_user_integrand(so, name)
+        desc = V.vegas_user_integrand.from_address(addr)
+        assert desc.dim == dim and desc.prepare and desc.launch
+        sizes.add(desc.args_bytes)
+    assert len(sizes) == 1 and sizes.pop() > 0
+    assert lib.vegas_set_user_integrand(None, addr, None) == V.VEGAS_EINVAL

@@ -90,18 +90,27 @@ def test_batch_fp32_close_to_fp64():
         assert abs(r32[1] / r64[1] - 1) < 0.01
 
 
-def test_graph_replay_equals_eager_run():
+@pytest.mark.parametrize("mode", [V.VEGAS_FP64, V.VEGAS_FP32_EVAL])
+def test_graph_replay_equals_eager_run(mode):
+    """A replayed graph reruns the same iterations.  The runs differ only in
+    the order of atomic additions: FP64 agrees to 1e-9 over six refinements.
+    In FP32 the shared histogram's float atomics from different warps land in
+    a run-dependent order and the refinements amplify that on the hard d=16
+    integral, so only the first (uniform-grid) iteration is compared there,
+    to 1e-6."""
     dims, ns, params = small_batch()
-    B = V.VegasBatch(dims, ns, 30, 13, V.VEGAS_FP32_EVAL, params, max_iters=8)
+    B = V.VegasBatch(dims, ns, 30, 13, mode, params, max_iters=8)
     B.run(6)
     eager = B.log()
     graph = B.capture(6)
+    upto = 6 if mode == V.VEGAS_FP64 else 1
+    rtol = 1e-9 if mode == V.VEGAS_FP64 else 1e-6
     for _ in range(2):
         graph.replay()
         torch.cuda.synchronize()
         replay = B.log()
         assert np.array_equal(replay[:, :6, 2], eager[:, :6, 2])
-        assert np.allclose(replay[:, :6, 4], eager[:, :6, 4], rtol=1e-6, atol=0)
+        assert np.allclose(replay[:, :upto, 4], eager[:, :upto, 4], rtol=rtol, atol=0)
         assert B.result(3)[3] == 6
     B.close()
 

@@ -242,3 +242,27 @@ def test_fp32_gauss_d8_close_to_fp64_gpu():
     assert abs(s32 / s64 - 1.0) < 0.01
     assert abs(m64 - erf(5.0) ** 8) < 4 * s64
     assert np.allclose(g32["edges"], g64["edges"], rtol=0, atol=1e-3)
+
+
+@pytest.mark.parametrize("mode", [V.VEGAS_FP64, V.VEGAS_FP32_EVAL])
+def test_pulls_over_seeds_are_standard_normal(mode):
+    """On a frozen adapted grid, (I - I_exact)/sigma over 200 seeds has mean ~0
+    and standard deviation ~1 (3-sigma bands of the sample moments)."""
+    dim, a = 4, 0.1
+    p = W.gauss_params(dim, a)
+    warm = V.Vegas(dim, 50, 999, V.VEGAS_FP64, W.GAUSS, p, max_iters=8)
+    warm.run([(200_000, 1)] * 6)
+    grid = warm.grid()
+    warm.close()
+    exact = float(erf(0.5 / a) ** dim)
+    pulls = []
+    for seed in range(200):
+        v = V.Vegas(dim, 50, seed, mode, W.GAUSS, p, max_iters=2)
+        v.set_grid(grid)
+        v.iterate(20_000, 0)
+        row = v.iterations()[0]
+        v.close()
+        pulls.append((row[4] - exact) / np.sqrt(row[5]))
+    pulls = np.array(pulls)
+    assert abs(pulls.mean()) < 3 / np.sqrt(200)
+    assert abs(pulls.std() - 1) < 3 / np.sqrt(2 * 200)
