@@ -64,9 +64,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="fp64,e2e,adjoint,batch,mix16",
+    ap.add_argument("--legs", default="fp64,e2e,adjoint,batch,mix16,gauss20",
                     help="measurements besides the headline FP32 steps (comma list of "
-                         "fp64, e2e, adjoint, batch, mix16; '' for none)")
+                         "fp64, e2e, adjoint, batch, mix16, gauss20; '' for none)")
     return ap.parse_args()
 
 
@@ -348,6 +348,35 @@ def mix16_timing(V, stream):
     return res
 
 
+def gauss20_timing(V, stream):
+    """The 20-dimensional symmetric Gaussian of Table 1 (Eq. 1, centres 1/2,
+    a = 0.1 as in the d=8 workload, 50 bins) on the d=8 workload's schedule:
+    10 adapting iterations of 1e7 samples, then 5 fixed-grid iterations of 1e8,
+    in both precisions; the result combines the fixed-grid iterations and is
+    compared with erf(5)^20."""
+    import torch
+
+    from paper_2002_12921_b300 import workloads as W
+
+    dim, a = 20, 0.1
+    exact = math.erf(0.5 / a) ** dim
+    res = {"exact": exact}
+    for name, mode in (("fp32", V.VEGAS_FP32_EVAL), ("fp64", V.VEGAS_FP64)):
+        v = V.Vegas(dim, NBINS, 20, mode, V.VEGAS_GAUSS, W.gauss_params(dim, a),
+                    max_iters=IT_ADAPT + IT_FIXED, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        v.run([(N_ADAPT, 1)] * IT_ADAPT + [(N_FIXED, 0)] * IT_FIXED, ALPHA)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        m, sg, c2, n, bad = v.result(IT_ADAPT)
+        v.close()
+        res[name] = {"ms": ms, "samples_per_s": SAMPLES_PER_STEP / (ms / 1e3), "mean": m,
+                     "sigma": sg, "chi2_dof": c2, "pull": (m - exact) / sg}
+    return res
+
+
 def e2e_mode(V, mode, steps, seed0, ws, stream):
     """Same workload through the public API with host buffers: per step the
     starting grid and the integrand parameters come from pinned host memory and
@@ -527,6 +556,7 @@ def main():
     adjoint = adjoint_timing(V, stream) if rank == 0 and "adjoint" in legs else None
     batch = batch_timing(V, stream) if rank == 0 and "batch" in legs else None
     mix16 = mix16_timing(V, stream) if rank == 0 and "mix16" in legs else None
+    gauss20 = gauss20_timing(V, stream) if rank == 0 and "gauss20" in legs else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -566,6 +596,7 @@ def main():
             "adjoint_d8_a0.15_1e8": adjoint,
             "batch_256_gauss_8iters": batch,
             "mix2_d16_N100_1e9_per_iter": mix16,
+            "symgauss_d20_a0.1_N50_10x1e7adapt+5x1e8fixed": gauss20,
             "result": result,
         }
         print(json.dumps(line), flush=True)

@@ -87,7 +87,7 @@ extern "C" {
 #define VEGAS_USER 5
 
 /* ---- limits --------------------------------------------------------------- */
-#define VEGAS_MAX_DIM 16
+#define VEGAS_MAX_DIM 20
 #define VEGAS_MAX_BINS 1024
 #define VEGAS_MAX_DIM_X_BINS 8192 /* dim * nbins (shared-memory grid copy) */
 
@@ -106,7 +106,7 @@ typedef struct {
 } vegas_config;
 
 /* Bytes of device workspace for a state of this shape with room for max_iters
- * iterations in its device log.  dim in [1, 16], nbins in [1, 1024],
+ * iterations in its device log.  dim in [1, 20], nbins in [1, 1024],
  * dim*nbins <= 8192, max_iters >= 1.  Returns VEGAS_EINVAL otherwise. */
 int vegas_workspace_bytes(int dim, int nbins, int max_iters, size_t *bytes);
 
@@ -168,7 +168,7 @@ int vegas_get_histogram(vegas_state *s, double *host_hist);
 /* Write the Philox4x32-10 words that samples i0 .. i0+n-1 of iteration iter
  * draw (the counter layout above) to d_out, n x dim uint32 rows in device
  * memory owned by the caller; the same device function the iterate kernel
- * uses.  A reproducibility and test aid.  dim in [1, 16]; asynchronous on the
+ * uses.  A reproducibility and test aid.  dim in [1, 20]; asynchronous on the
  * stream. */
 int vegas_sample_words(uint64_t seed, uint32_t integral_id, uint32_t iter, uint64_t i0,
                        uint64_t n, int dim, uint32_t *d_out, void *cuda_stream);
@@ -218,7 +218,7 @@ int vegas_gauss_adjoint(vegas_state *s, const double *params, int nparams, uint3
 
 /* ---- many integrals in one persistent launch ------------------------------ */
 /* A batch holds `count` independent Eq. 1 Gaussian integrals (VegasFlow
- * Sec. 3.1) of their own dimension (1..16) and samples per iteration, all with
+ * Sec. 3.1) of their own dimension (1..20) and samples per iteration, all with
  * nbins bins per dimension, sharing one seed and one iteration schedule.
  * Integral b draws its samples with integral_id = b in the counter (see the
  * top of this file), so its result equals that of a single vegas_state run

@@ -83,11 +83,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
-def build_user_integrand(src: str, out: str, force: bool = False, verbose: bool = False) -> str:
-    """Compile a caller's integrand file (one that uses VEGAS_USER_INTEGRAND of
-    include/vegas_user_integrand.cuh) into the shared library `out`, with the
-    library's own architecture and flags, if it is missing or older than its
-    source or the library's headers.  Returns `out`."""
+def build_module(src: str, out: str, force: bool = False, verbose: bool = False) -> str:
+    """Compile one CUDA source file into the shared library `out` with the
+    library's architecture and flags (include/ on the include path), if it is
+    missing or older than its source or the library's headers.  Returns `out`."""
     if force or _stale(out, [src] + headers()):
         os.makedirs(os.path.dirname(os.path.abspath(out)), exist_ok=True)
         tmp = out + f".tmp{os.getpid()}"
@@ -100,6 +99,12 @@ def build_user_integrand(src: str, out: str, force: bool = False, verbose: bool 
             sys.stderr.write(f"== {os.path.basename(src)}\n{r.stderr}")
         os.replace(tmp, out)
     return out
+
+
+def build_user_integrand(src: str, out: str, force: bool = False, verbose: bool = False) -> str:
+    """Compile a caller's integrand file (one that uses VEGAS_USER_INTEGRAND of
+    include/vegas_user_integrand.cuh) into the shared library `out`."""
+    return build_module(src, out, force, verbose)
 
 
 if __name__ == "__main__":

@@ -159,12 +159,14 @@ const void* adjoint_kernel(int mode, int dim, bool grad) {
         ADJ_ROW(float, 1),  ADJ_ROW(float, 2),  ADJ_ROW(float, 3),  ADJ_ROW(float, 4),
         ADJ_ROW(float, 5),  ADJ_ROW(float, 6),  ADJ_ROW(float, 7),  ADJ_ROW(float, 8),
         ADJ_ROW(float, 9),  ADJ_ROW(float, 10), ADJ_ROW(float, 11), ADJ_ROW(float, 12),
-        ADJ_ROW(float, 13), ADJ_ROW(float, 14), ADJ_ROW(float, 15), ADJ_ROW(float, 16)};
+        ADJ_ROW(float, 13), ADJ_ROW(float, 14), ADJ_ROW(float, 15), ADJ_ROW(float, 16),
+        ADJ_ROW(float, 17), ADJ_ROW(float, 18), ADJ_ROW(float, 19), ADJ_ROW(float, 20)};
     static const void* const f64[kMaxDim][2] = {
         ADJ_ROW(double, 1),  ADJ_ROW(double, 2),  ADJ_ROW(double, 3),  ADJ_ROW(double, 4),
         ADJ_ROW(double, 5),  ADJ_ROW(double, 6),  ADJ_ROW(double, 7),  ADJ_ROW(double, 8),
         ADJ_ROW(double, 9),  ADJ_ROW(double, 10), ADJ_ROW(double, 11), ADJ_ROW(double, 12),
-        ADJ_ROW(double, 13), ADJ_ROW(double, 14), ADJ_ROW(double, 15), ADJ_ROW(double, 16)};
+        ADJ_ROW(double, 13), ADJ_ROW(double, 14), ADJ_ROW(double, 15), ADJ_ROW(double, 16),
+        ADJ_ROW(double, 17), ADJ_ROW(double, 18), ADJ_ROW(double, 19), ADJ_ROW(double, 20)};
     return (mode == VEGAS_FP32_EVAL ? f32 : f64)[dim - 1][grad ? 1 : 0];
 }
 

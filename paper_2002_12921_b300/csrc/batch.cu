@@ -11,6 +11,7 @@
 #include "batch_kernel.cuh"
 #include "philox.cuh"
 #include "refine_row.cuh"
+#include "stage.cuh"
 
 namespace vegas {
 namespace {
@@ -26,6 +27,8 @@ struct BatchRow {
 struct PostArgs {
     const BatchRow* rows;
     const BatchInfo* info;
+    const FnConsts* consts;
+    float2* staged32;  // float path: staged pairs of every row (hist layout), else null
     double* edges;
     double* hist;
     double* acc;
@@ -47,9 +50,16 @@ __global__ void __launch_bounds__(kPostThreads) batch_post_kernel(const PostArgs
     const BatchRow row = a.rows[blockIdx.x];
     const BatchInfo info = a.info[row.b];
     const int N = a.nbins;
-    if (a.adapt)
-        refine_row(a.edges + info.edge_off + (size_t)row.k * (N + 1),
-                   a.hist + info.hist_off + (size_t)row.k * N, N, a.alpha, sm, sbuf);
+    if (a.adapt) {
+        double* e = a.edges + info.edge_off + (size_t)row.k * (N + 1);
+        refine_row(e, a.hist + info.hist_off + (size_t)row.k * N, N, a.alpha, sm, sbuf);
+        if (a.staged32) {  // the float path's pairs of the new grid row
+            __syncthreads();
+            const FnConsts& fc = a.consts[row.b];
+            stage_row32(e, N, fc.sc[1][row.k], fc.sh[1][row.k],
+                        a.staged32 + info.hist_off + (size_t)row.k * N);
+        }
+    }
     if (row.k == 0 && threadIdx.x == 0) {
         double* acc = a.acc + 4 * (size_t)row.b;
         double* L = a.log + ((size_t)row.b * a.max_iters + a.iter) * kLogStride;
@@ -85,11 +95,23 @@ __global__ void batch_init_kernel(double* edges, size_t n_edges, double* hist, s
     for (size_t i = tid; i < (size_t)kCtrlWords; i += nth) ctrl[i] = 0u;
 }
 
+// The float path's staged pairs of every (integral, dimension) row, block r
+// taking row r (after the grids are reset).
+__global__ void batch_stage_kernel(const BatchRow* rows, const BatchInfo* info,
+                                   const FnConsts* consts, const double* edges, float2* staged,
+                                   int nbins) {
+    const BatchRow row = rows[blockIdx.x];
+    const BatchInfo in = info[row.b];
+    const FnConsts& fc = consts[row.b];
+    stage_row32(edges + in.edge_off + (size_t)row.k * (nbins + 1), nbins, fc.sc[1][row.k],
+                fc.sh[1][row.k], staged + in.hist_off + (size_t)row.k * nbins);
+}
+
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct BatchLayout {
-    size_t edges, hist, acc, log, consts, info, rows, tiles, ctrl, total;
+    size_t edges, hist, acc, log, consts, info, rows, tiles, ctrl, staged, total;
     size_t n_edges, n_hist, n_rows, max_tiles;
 };
 
@@ -124,6 +146,7 @@ BatchLayout batch_layout(int count, const int* dims, const uint64_t* n, int nbin
     L.rows = off;  off = align_up(off + L.n_rows * sizeof(BatchRow));
     L.tiles = off; off = align_up(off + L.max_tiles * sizeof(BatchTile));
     L.ctrl = off;  off = align_up(off + kCtrlWords * sizeof(unsigned));
+    L.staged = off; off = align_up(off + L.n_hist * sizeof(float2));
     L.total = off;
     return L;
 }
@@ -203,7 +226,15 @@ int launch_batch_init(vegas_batch* b) {
         at<double>(b, L.log), (size_t)b->count * b->max_iters * kLogStride,
         at<unsigned>(b, L.ctrl), b->nbins);
     b->iters = 0;
-    return e == cudaSuccess ? VEGAS_OK : VEGAS_ECUDA;
+    if (e != cudaSuccess) return VEGAS_ECUDA;
+    if (b->mode == VEGAS_FP32_EVAL &&
+        launch_kernel(batch_stage_kernel, dim3((unsigned)L.n_rows), dim3(64), 0, b->stream,
+                      (const BatchRow*)at<BatchRow>(b, L.rows),
+                      (const BatchInfo*)at<BatchInfo>(b, L.info),
+                      (const FnConsts*)at<FnConsts>(b, L.consts), (const double*)at<double>(b, L.edges),
+                      at<float2>(b, L.staged), b->nbins) != cudaSuccess)
+        return VEGAS_ECUDA;
+    return VEGAS_OK;
 }
 
 }  // namespace
@@ -355,6 +386,7 @@ int vegas_batch_iterate(vegas_batch* b, int adapt, double alpha) {
     a.nbins = b->nbins;
     a.max_dim = b->max_dim;
     a.hist_log2r = ad ? hist_log2r(b->mode, b->max_dim, b->nbins) : 0;
+    a.staged32 = b->mode == VEGAS_FP32_EVAL ? at<float2>(b, L.staged) : nullptr;
     std::memcpy(a.rk0, b->rk0, sizeof(a.rk0));
     std::memcpy(a.rk1, b->rk1, sizeof(a.rk1));
 
@@ -380,6 +412,8 @@ int vegas_batch_iterate(vegas_batch* b, int adapt, double alpha) {
     PostArgs pa;
     pa.rows = at<BatchRow>(b, L.rows);
     pa.info = a.info;
+    pa.consts = a.consts;
+    pa.staged32 = a.staged32 ? at<float2>(b, L.staged) : nullptr;
     pa.edges = a.edges;
     pa.hist = a.hist;
     pa.acc = a.acc;

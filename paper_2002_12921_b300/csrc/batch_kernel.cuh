@@ -42,6 +42,7 @@ struct BatchArgs {
     int nbins;
     int max_dim;
     int hist_log2r;
+    const float2* staged32;  // float path: staged pairs of every row (hist layout), else null
     unsigned rk0[10], rk1[10];
 };
 
@@ -55,7 +56,8 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchTile& 
     const int logr = ADAPT ? a.hist_log2r : 0;
     const FnConsts& fc = a.consts[t.b];
     const BatchInfo info = a.info[t.b];
-    stage_grid<R, D, ADAPT>(a.edges + info.edge_off, N, logr, fc, sgrid, shist);
+    stage_grid<R, D, ADAPT>(a.edges + info.edge_off, N, logr, fc, sgrid, shist,
+                            a.staged32 ? a.staged32 + info.hist_off : nullptr);
     R n4, nlast;
     jacobian_factors<R, D>(N, n4, nlast);
     __syncthreads();
@@ -104,6 +106,7 @@ __global__ void __launch_bounds__(256) batch_iterate_kernel(const BatchArgs a) {
             VEGAS_BATCH_CASE(5) VEGAS_BATCH_CASE(6) VEGAS_BATCH_CASE(7) VEGAS_BATCH_CASE(8)
             VEGAS_BATCH_CASE(9) VEGAS_BATCH_CASE(10) VEGAS_BATCH_CASE(11) VEGAS_BATCH_CASE(12)
             VEGAS_BATCH_CASE(13) VEGAS_BATCH_CASE(14) VEGAS_BATCH_CASE(15) VEGAS_BATCH_CASE(16)
+            VEGAS_BATCH_CASE(17) VEGAS_BATCH_CASE(18) VEGAS_BATCH_CASE(19) VEGAS_BATCH_CASE(20)
 #undef VEGAS_BATCH_CASE
             default: __syncthreads(); break;
         }

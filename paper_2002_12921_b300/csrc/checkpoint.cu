@@ -136,6 +136,7 @@ extern "C" int vegas_import_state(vegas_state** out, const void* buf, size_t byt
     if (rc == VEGAS_OK &&
         (cudaMemcpyAsync(s->edges, p, 8 * dim * (nbins + 1), cudaMemcpyHostToDevice,
                          s->stream) != cudaSuccess ||
+         restage(s) != VEGAS_OK ||
          cudaMemcpyAsync(s->hist, p + 8 * dim * (nbins + 1), 8 * dim * nbins,
                          cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
          (n_iter && cudaMemcpyAsync(s->log, p + 8 * (dim * (nbins + 1) + dim * nbins),

@@ -24,6 +24,7 @@
 #include <stdint.h>
 
 #include "philox.cuh"
+#include "stage.cuh"
 #include "vegas_internal.h"
 
 // launch-shape tuning: minimum resident blocks the register allocation
@@ -192,9 +193,7 @@ struct Prec<float> {
     static constexpr int kStage = 1;  // FnConsts staging index
     // (sc e' + sh, sc Delta) computed in double, rounded once
     static __device__ __forceinline__ Pair pair(double e0, double e1, double sc, double sh) {
-        const double w = e1 - e0;
-        const double e = ::fma(-0x1.fffffep-1, w, e0);
-        return make_float2((float)::fma(e, sc, sh), (float)(w * sc));
+        return stage_pair32(e0, e1, sc, sh);
     }
     static __device__ __forceinline__ bool finite(float v) { return fabsf(v) <= FLT_MAX; }
     static __device__ __forceinline__ float fma(float x, float y, float z) { return fmaf(x, y, z); }
@@ -337,12 +336,19 @@ struct Acc<double> {
 template <typename R, int D, bool ADAPT>
 __device__ __forceinline__ void stage_grid(const double* __restrict__ edges, int N, int logr,
                                            const FnConsts& fc, typename Prec<R>::Pair* sgrid,
-                                           typename Prec<R>::Hist* shist) {
+                                           typename Prec<R>::Hist* shist,
+                                           const float2* __restrict__ staged32 = nullptr) {
     using P = Prec<R>;
-    for (int idx = threadIdx.x; idx < D * N; idx += blockDim.x) {
-        const int k = idx / N, j = idx - k * N;
-        const double* e = edges + (size_t)k * (N + 1) + j;
-        sgrid[idx] = P::pair(e[0], e[1], fc.sc[P::kStage][k], fc.sh[P::kStage][k]);
+    if (sizeof(R) == 4 && staged32 != nullptr) {
+        // float path with the pairs already staged by the last grid change
+        for (int idx = threadIdx.x; idx < D * N; idx += blockDim.x)
+            reinterpret_cast<float2*>(sgrid)[idx] = staged32[idx];
+    } else {
+        for (int idx = threadIdx.x; idx < D * N; idx += blockDim.x) {
+            const int k = idx / N, j = idx - k * N;
+            const double* e = edges + (size_t)k * (N + 1) + j;
+            sgrid[idx] = P::pair(e[0], e[1], fc.sc[P::kStage][k], fc.sh[P::kStage][k]);
+        }
     }
     if (ADAPT)
         for (int idx = threadIdx.x; idx < (D * N) << logr; idx += blockDim.x)
@@ -491,7 +497,7 @@ __device__ __forceinline__ void iterate_body(const IterArgs& a) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctrl[kStatus], kStatusLogFull);
         return;
     }
-    stage_grid<R, D, ADAPT>(a.edges, N, logr, a.fc, sgrid, shist);
+    stage_grid<R, D, ADAPT>(a.edges, N, logr, a.fc, sgrid, shist, a.staged32);
 
     // Pre-scale of the float path: f J is carried as f J 2^-h with 2^h near the
     // previous iteration's estimate; the prefactor enters the Jacobian's start.
@@ -605,7 +611,8 @@ __global__ void VEGAS_ITERATE_BOUNDS vegas_user_iterate_kernel(const IterArgs a)
             VEGAS_KERNEL_ROW(R, FN, 7),  VEGAS_KERNEL_ROW(R, FN, 8),  VEGAS_KERNEL_ROW(R, FN, 9),  \
             VEGAS_KERNEL_ROW(R, FN, 10), VEGAS_KERNEL_ROW(R, FN, 11), VEGAS_KERNEL_ROW(R, FN, 12), \
             VEGAS_KERNEL_ROW(R, FN, 13), VEGAS_KERNEL_ROW(R, FN, 14), VEGAS_KERNEL_ROW(R, FN, 15), \
-            VEGAS_KERNEL_ROW(R, FN, 16)};                                                     \
+            VEGAS_KERNEL_ROW(R, FN, 16), VEGAS_KERNEL_ROW(R, FN, 17), VEGAS_KERNEL_ROW(R, FN, 18), \
+            VEGAS_KERNEL_ROW(R, FN, 19), VEGAS_KERNEL_ROW(R, FN, 20)};                        \
         if (dim < 1 || dim > kMaxDim) return nullptr;                                         \
         return table[dim - 1][adapt ? 1 : 0];                                                 \
     }                                                                                         \

@@ -143,12 +143,14 @@ const void* noalloc_kernel(int mode, int dim, bool adapt) {
         NA_ROW(float, 1),  NA_ROW(float, 2),  NA_ROW(float, 3),  NA_ROW(float, 4),
         NA_ROW(float, 5),  NA_ROW(float, 6),  NA_ROW(float, 7),  NA_ROW(float, 8),
         NA_ROW(float, 9),  NA_ROW(float, 10), NA_ROW(float, 11), NA_ROW(float, 12),
-        NA_ROW(float, 13), NA_ROW(float, 14), NA_ROW(float, 15), NA_ROW(float, 16)};
+        NA_ROW(float, 13), NA_ROW(float, 14), NA_ROW(float, 15), NA_ROW(float, 16),
+        NA_ROW(float, 17), NA_ROW(float, 18), NA_ROW(float, 19), NA_ROW(float, 20)};
     static const void* const f64[kMaxDim][2] = {
         NA_ROW(double, 1),  NA_ROW(double, 2),  NA_ROW(double, 3),  NA_ROW(double, 4),
         NA_ROW(double, 5),  NA_ROW(double, 6),  NA_ROW(double, 7),  NA_ROW(double, 8),
         NA_ROW(double, 9),  NA_ROW(double, 10), NA_ROW(double, 11), NA_ROW(double, 12),
-        NA_ROW(double, 13), NA_ROW(double, 14), NA_ROW(double, 15), NA_ROW(double, 16)};
+        NA_ROW(double, 13), NA_ROW(double, 14), NA_ROW(double, 15), NA_ROW(double, 16),
+        NA_ROW(double, 17), NA_ROW(double, 18), NA_ROW(double, 19), NA_ROW(double, 20)};
     return (mode == VEGAS_FP32_EVAL ? f32 : f64)[dim - 1][adapt ? 1 : 0];
 }
 
@@ -239,7 +241,7 @@ extern "C" int vegas_iterate_noalloc(double* d_edges, int dim, int nbins, uint64
     if (cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(256), args, smem, stream) != cudaSuccess)
         return VEGAS_ECUDA;
     if (ad) {
-        RefineArgs r;
+        RefineArgs r{};  // no staged pairs: this path stages in the iterate kernel
         r.edges = d_edges;
         r.hist = a.hist;
         r.dim = dim;

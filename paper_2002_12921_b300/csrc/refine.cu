@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "refine_row.cuh"
+#include "stage.cuh"
 #include "vegas_internal.h"
 
 namespace vegas {
@@ -29,7 +30,25 @@ __global__ void __launch_bounds__(kRefineThreads) refine_kernel(const RefineArgs
     __shared__ double sbuf[33];
     const int N = a.nbins;
     const int k = blockIdx.x;
-    refine_row(a.edges + (size_t)k * (N + 1), a.hist + (size_t)k * N, N, a.alpha, sm, sbuf);
+    double* e = a.edges + (size_t)k * (N + 1);
+    refine_row(e, a.hist + (size_t)k * N, N, a.alpha, sm, sbuf);
+    if (a.staged32) {  // the float path's pairs of the new grid
+        __syncthreads();
+        stage_row32(e, N, a.sc32[k], a.sh32[k], a.staged32 + (size_t)k * N);
+    }
+}
+
+struct Stage32Args {
+    const double* edges;
+    float2* staged;
+    int nbins;
+    double sc[kMaxDim], sh[kMaxDim];
+};
+
+// The float path's staged pairs of the current grid, one block per dimension.
+__global__ void stage32_kernel(const Stage32Args a) {
+    const int k = blockIdx.x, N = a.nbins;
+    stage_row32(a.edges + (size_t)k * (N + 1), N, a.sc[k], a.sh[k], a.staged + (size_t)k * N);
 }
 
 // Uniform grid e_l = l/N, cleared histogram, log and control words.
@@ -71,6 +90,19 @@ cudaError_t launch_shard_row(double* row, const double* totals, unsigned long lo
 cudaError_t launch_refine(const RefineArgs& a, cudaStream_t stream) {
     const size_t smem = (size_t)(4 * a.nbins + 2) * sizeof(double);
     return launch_kernel(refine_kernel, dim3(a.dim), dim3(kRefineThreads), smem, stream, a);
+}
+
+cudaError_t launch_stage32(const double* edges, float2* staged, int dim, int nbins,
+                           const FnConsts& fc, cudaStream_t stream) {
+    Stage32Args a;
+    a.edges = edges;
+    a.staged = staged;
+    a.nbins = nbins;
+    for (int k = 0; k < kMaxDim; ++k) {
+        a.sc[k] = fc.sc[1][k];
+        a.sh[k] = fc.sh[1][k];
+    }
+    return launch_kernel(stage32_kernel, dim3(dim), dim3(128), 0, stream, a);
 }
 
 cudaError_t launch_init(double* edges, double* hist, double* log, unsigned* ctrl, int dim,

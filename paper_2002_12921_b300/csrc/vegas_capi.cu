@@ -202,7 +202,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t edges, hist, log, partials, ctrl, total;
+    size_t edges, hist, log, partials, ctrl, staged, total;
 };
 
 Layout layout(int dim, int nbins, int max_iters) {
@@ -218,6 +218,8 @@ Layout layout(int dim, int nbins, int max_iters) {
     off = align_up(off + (size_t)kMaxGrid * kPartialStride * sizeof(double));
     L.ctrl = off;
     off = align_up(off + kCtrlWords * sizeof(unsigned));
+    L.staged = off;  // float path: staged pairs of the grid
+    off = align_up(off + (size_t)dim * nbins * sizeof(float2));
     L.total = off;
     return L;
 }
@@ -247,6 +249,17 @@ const void* kernel_for(const vegas_state* s, bool adapt) {
     return s->mode == VEGAS_FP32_EVAL ? iterate_kernel_f32(s->integrand, s->dim, adapt)
                                       : iterate_kernel_f64(s->integrand, s->dim, adapt);
 }
+
+}  // namespace
+
+// After any change of the grid other than a refinement (which stages its own
+// result): rewrite the float path's staged pairs.  Enqueued on the stream.
+int restage(vegas_state* s) {
+    if (!s->staged32) return VEGAS_OK;
+    return cuda_status(launch_stage32(s->edges, s->staged32, s->dim, s->nbins, s->fc, s->stream));
+}
+
+namespace {
 
 void default_config(vegas_config* c) {
     c->block_threads = 256;
@@ -317,9 +330,12 @@ int vegas_init_grid(vegas_state** out, int dim, int nbins, uint64_t seed, int mo
     s->log = reinterpret_cast<double*>(s->ws + L.log);
     s->partials = reinterpret_cast<double*>(s->ws + L.partials);
     s->ctrl = reinterpret_cast<unsigned*>(s->ws + L.ctrl);
+    s->staged32 =
+        mode == VEGAS_FP32_EVAL ? reinterpret_cast<float2*>(s->ws + L.staged) : nullptr;
 
     rc = cuda_status(launch_init(s->edges, s->hist, s->log, s->ctrl, dim, nbins, max_iters,
                                  s->stream));
+    if (rc == VEGAS_OK) rc = restage(s);
     if (rc != VEGAS_OK) { delete s; return rc; }
     *out = s;
     return VEGAS_OK;
@@ -400,6 +416,7 @@ static int enqueue_iteration(vegas_state* s, uint64_t begin, uint64_t end, int a
     std::memcpy(a.rk0, s->rk0, sizeof(a.rk0));
     std::memcpy(a.rk1, s->rk1, sizeof(a.rk1));
     a.fc = s->fc;
+    a.staged32 = s->staged32;
 
     for (uint64_t i0 = begin; i0 < end; i0 += chunk) {
         const uint64_t nc = (end - i0) < chunk ? (end - i0) : chunk;
@@ -480,12 +497,17 @@ int vegas_refine(vegas_state* s, double alpha) {
     if (!s || !(alpha >= 0.0) || !std::isfinite(alpha)) return VEGAS_EINVAL;
     DeviceGuard g(s->device);
     if (!g.ok) return VEGAS_ECUDA;
-    RefineArgs r;
+    RefineArgs r{};
     r.edges = s->edges;
     r.hist = s->hist;
     r.dim = s->dim;
     r.nbins = s->nbins;
     r.alpha = alpha;
+    r.staged32 = s->staged32;
+    for (int k = 0; k < kMaxDim; ++k) {
+        r.sc32[k] = s->fc.sc[1][k];
+        r.sh32[k] = s->fc.sh[1][k];
+    }
     return cuda_status(launch_refine(r, s->stream));
 }
 
@@ -579,6 +601,8 @@ int vegas_set_grid(vegas_state* s, const double* host_edges) {
     if (cudaMemcpyAsync(s->edges, host_edges, bytes, cudaMemcpyHostToDevice, s->stream) !=
         cudaSuccess)
         return VEGAS_ECUDA;
+    const int rc = restage(s);
+    if (rc != VEGAS_OK) return rc;
     return cuda_status(cudaStreamSynchronize(s->stream));
 }
 

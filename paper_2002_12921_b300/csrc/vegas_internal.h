@@ -89,13 +89,16 @@ struct IterArgs {
     unsigned integral_id;
     unsigned rk0[10], rk1[10];  // Philox round keys k + r W
     FnConsts fc;
+    const float2* staged32;     // float path: the grid's staged pairs (dim x N), or null
 };
 
 struct RefineArgs {
-    double* edges;  // dim x (N+1), refined in place
-    double* hist;   // dim x N, cleared
-    int dim, nbins;
-    double alpha;
+    double* edges = nullptr;  // dim x (N+1), refined in place
+    double* hist = nullptr;   // dim x N, cleared
+    int dim = 0, nbins = 0;
+    double alpha = 0.0;
+    float2* staged32 = nullptr;  // float path: the refined grid's staged pairs (dim x N), or null
+    double sc32[kMaxDim] = {}, sh32[kMaxDim] = {};  // the float staging transform
 };
 
 // Kernel lookup: the iterate kernel for (mode, integrand, dim, adapt), or
@@ -110,6 +113,9 @@ int hist_log2r(int mode, int dim, int nbins);
 size_t iterate_smem_bytes(int mode, int dim, int nbins, bool adapt, int log2r);
 
 cudaError_t launch_refine(const RefineArgs& a, cudaStream_t stream);
+// The float path's staged pairs (dim x N) of the grid `edges` (refine.cu).
+cudaError_t launch_stage32(const double* edges, float2* staged, int dim, int nbins,
+                           const FnConsts& fc, cudaStream_t stream);
 void combine_rows(const double* rows, int stride, int first_iter, int n, double* mean,
                   double* sigma, double* chi2_dof);
 // Install summed shard totals {S1, S2, nonfinite} into a log row with I, var
@@ -142,5 +148,10 @@ struct vegas_state {
     double params[1 + 2 * VEGAS_MAX_DIM];  // the integrand parameters as given
     int nparams;
     vegas_user_integrand user;  // VEGAS_USER: the caller's kernels (launch == NULL: unset)
+    float2* staged32;  // VEGAS_FP32_EVAL: the grid's staged pairs in the workspace, else null
 };
+
+// Rewrite a float-path state's staged pairs after its edges changed other than
+// by vegas_refine (enqueued on the state's stream; VEGAS_OK for FP64 states).
+int restage(vegas_state* s);
 

@@ -36,7 +36,7 @@ def test_workspace_bytes_validation(lib):
     b = V.vegas_workspace_bytes(8, 50, 64)
     assert b % 256 == 0 and b >= 8 * 51 * 8 + 8 * 50 * 8 + 64 * 8 * 8
     assert V.vegas_workspace_bytes(16, 512, 1) > V.vegas_workspace_bytes(16, 100, 1)
-    for args in [(0, 50, 1), (17, 50, 1), (8, 0, 1), (8, 1025, 1), (16, 600, 1), (8, 50, 0)]:
+    for args in [(0, 50, 1), (21, 50, 1), (8, 0, 1), (8, 1025, 1), (16, 600, 1), (8, 50, 0)]:
         with pytest.raises(V.VegasError) as e:
             V.vegas_workspace_bytes(*args)
         assert e.value.status == V.VEGAS_EINVAL
