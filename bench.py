@@ -43,7 +43,7 @@ ALU_PEAK_TOPS = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
 
 # DRAM bytes per launch of the fixed-grid FP32 iterate kernel from the ncu
 # capture summarised in profiles/ (None until captured for this kernel build).
-ITERATE_TRAFFIC_BYTES = 60672  # dram read 60.7 KB + write 0 (this kernel build)
+ITERATE_TRAFFIC_BYTES = 66048  # dram read 66.0 KB + write 0 per 1e8-sample launch (ncu, this kernel build)
 
 
 def alg_ops_per_sample(d):
