@@ -59,7 +59,7 @@ def alg_ops_per_sample(d):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fp64-steps", type=int, default=2)
@@ -78,23 +78,42 @@ def dist_env():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons while it runs."""
+    """nvidia-smi sampling of SM clocks and throttle reasons every 50 ms while it
+    runs; each row is stamped with the host time it arrived, so that the summary
+    covers only the rows inside a given window (the timed region)."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_index):
-        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        import threading
+
+        self.rows = []
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100", "-i", str(device_index)], stdout=self.file,
-                stderr=subprocess.DEVNULL)
+                 "-lms", "50", "-i", str(device_index)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
 
-    def stop(self):
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append((time.time(), parts))
+
+    def wait_ready(self, timeout=5.0):
+        """Block until the sampler has produced a row (or `timeout` seconds)."""
+        t_end = time.time() + timeout
+        while self.proc is not None and not self.rows and time.time() < t_end:
+            time.sleep(0.01)
+
+    def stop(self, window=None):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -102,16 +121,16 @@ class Clocks:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        self.file.flush()
-        rows = []
-        with open(self.file.name) as fh:
-            for line in fh:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) == 8:
-                    rows.append(parts)
-        os.unlink(self.file.name)
+        self.reader.join(timeout=5)
+        rows = self.rows
+        if window is not None:
+            t0, t1 = window
+            inside = [r for r in rows if t0 <= r[0] <= t1]
+            rows = inside
+        rows = [r for _, r in rows]
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples in window"],
+                    "samples": 0}
 
         def num(x):
             try:
@@ -204,6 +223,7 @@ def time_mode(V, mode, steps, warmup, seed0, ws, flush, stream, world=1):
     for w in range(warmup):
         handles.append(step(seed0 + 1000 + w))
     torch.cuda.synchronize()
+    time_mode.window_start = time.time()
     step_events, fixed = [], []
     for s in range(steps):
         l2_flush(flush)
@@ -213,6 +233,7 @@ def time_mode(V, mode, steps, warmup, seed0, ws, flush, stream, world=1):
         e1.record(stream)
         step_events.append((e0, e1))
     torch.cuda.synchronize()
+    time_mode.window_end = time.time()
     ms = [a.elapsed_time(b) for a, b in step_events]
     fixed_ms = [a.elapsed_time(b) for a, b in fixed]
     last = handles[-1]
@@ -509,11 +530,12 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(torch.cuda.current_device())
+    clocks.wait_ready()
     # N > 1: one integral sharded over the ranks (same seed everywhere)
     seed_main = 2 if world > 1 else seed0
     ms32, fixed32, res32 = time_mode(V, V.VEGAS_FP32_EVAL, args.steps, max(3, args.warmup),
                                      seed_main, ws, flush, stream, world)
-    clk = clocks.stop()
+    clk = clocks.stop((time_mode.window_start, time_mode.window_end))
     total_ms = sum(ms32)
     if dist:
         t = torch.tensor([total_ms], device="cuda")

@@ -28,19 +28,25 @@
 #include "vegas_internal.h"
 
 // launch-shape tuning: minimum resident blocks the register allocation
-// targets, and samples per unrolled loop step
+// targets
 #ifdef VEGAS_ITERATE_MIN_BLOCKS
 #define VEGAS_ITERATE_BOUNDS __launch_bounds__(256, VEGAS_ITERATE_MIN_BLOCKS)
 #else
 #define VEGAS_ITERATE_BOUNDS __launch_bounds__(256)
 #endif
-#ifndef VEGAS_SAMPLE_UNROLL
-#define VEGAS_SAMPLE_UNROLL 1
-#endif
 
 namespace vegas {
 
-constexpr int kSampleUnroll = VEGAS_SAMPLE_UNROLL;
+// Samples per unrolled step of the sample loop.  Measured: two samples per
+// step speed up the double kernels (d=8 Gaussian: fixed grid 8.49 -> 8.21 ms
+// per 1e8, adapting 1.09 -> 1.06 ms per 1e7; 256-integral batch 61.5 -> 58.1
+// ms) but slow the float ones (d=8 fixed grid 748 -> 773 us per 1e8; d=16
+// mixture, adapting, 3.64e10 -> 3.29e10 samples/s; batch 7.95 -> 9.03 ms),
+// whose integer-multiply pipe is already the busiest unit.
+template <typename R>
+constexpr int sample_unroll() {
+    return sizeof(R) == 8 ? 2 : 1;
+}
 
 // 2^x with the hardware exponential (flush-to-zero for tiny results).
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -376,7 +382,8 @@ __device__ __forceinline__ void sample_loop(unsigned long long first, unsigned l
     PhiloxCallConst pc[DC];
 #pragma unroll
     for (int q = 0; q < DC; ++q) pc[q] = philox_call_const(c2base | (uint32_t)q, cur_hi, rk0, rk1);
-#pragma unroll kSampleUnroll
+    constexpr int kUnroll = sample_unroll<R>();
+#pragma unroll kUnroll
     for (unsigned long long i = first; i < end; i += stride) {
         const uint32_t i_lo = (uint32_t)i, i_hi = (uint32_t)(i >> 32);
         if (i_hi != cur_hi) {  // crossing a multiple of 2^32: rare
