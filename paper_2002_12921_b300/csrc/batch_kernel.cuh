@@ -53,7 +53,15 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchTile& 
                                            typename Prec<R>::Hist* shist, double* sred,
                                            unsigned* sbad) {
     const int N = a.nbins;
-    const int logr = ADAPT ? a.hist_log2r : 0;
+    // Histogram copies: the shared memory is sized for the widest integral
+    // with 2^hist_log2r copies; a tile of fewer dimensions takes as many
+    // copies as fit in it, up to one per lane (lanes of a warp that share a
+    // copy make the shared atomics retry).
+    int logr = 0;
+    if (ADAPT) {
+        logr = a.hist_log2r;
+        while (logr < 5 && (D << (logr + 1)) <= (a.max_dim << a.hist_log2r)) ++logr;
+    }
     const FnConsts& fc = a.consts[t.b];
     const BatchInfo info = a.info[t.b];
     stage_grid<R, D, ADAPT>(a.edges + info.edge_off, N, logr, fc, sgrid, shist,
