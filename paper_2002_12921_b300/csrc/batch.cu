@@ -424,7 +424,8 @@ int vegas_batch_iterate(vegas_batch* b, int adapt, double alpha) {
     pa.iter = (unsigned)b->iters;
     pa.adapt = ad ? 1 : 0;
     pa.alpha = alpha;
-    if (launch_kernel(batch_post_kernel, dim3((unsigned)L.n_rows), dim3(kPostThreads),
+    if (launch_kernel(batch_post_kernel, dim3((unsigned)L.n_rows),
+                      dim3(refine_threads(b->nbins, kPostThreads)),
                       (size_t)(4 * b->nbins + 2) * sizeof(double), b->stream, pa) !=
         cudaSuccess)
         return VEGAS_ECUDA;

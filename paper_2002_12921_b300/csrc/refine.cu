@@ -89,7 +89,8 @@ cudaError_t launch_shard_row(double* row, const double* totals, unsigned long lo
 
 cudaError_t launch_refine(const RefineArgs& a, cudaStream_t stream) {
     const size_t smem = (size_t)(4 * a.nbins + 2) * sizeof(double);
-    return launch_kernel(refine_kernel, dim3(a.dim), dim3(kRefineThreads), smem, stream, a);
+    return launch_kernel(refine_kernel, dim3(a.dim), dim3(refine_threads(a.nbins, kRefineThreads)),
+                         smem, stream, a);
 }
 
 cudaError_t launch_stage32(const double* edges, float2* staged, int dim, int nbins,

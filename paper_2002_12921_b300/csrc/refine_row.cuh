@@ -26,10 +26,21 @@ __device__ __forceinline__ double block_sum_all(double v, double* sbuf) {
     return sbuf[32];
 }
 
+// Threads per block for refining rows of N bins: one per bin, in whole warps,
+// at most `max_threads` (the rows are short and every phase ends in a block
+// barrier, so idle warps only add to each barrier's wait).
+inline int refine_threads(int N, int max_threads) {
+    const int t = (N + 31) / 32 * 32;
+    return t < 32 ? 32 : (t > max_threads ? max_threads : t);
+}
+
 __device__ __forceinline__ double damp(double r, double alpha) {
     if (r <= 0.0) return 0.0;
     if (r == 1.0) return 1.0;
-    return pow((r - 1.0) / log(r), alpha);
+    const double x = (r - 1.0) / log(r);
+    // the usual alpha = 3/2 as x sqrt(x): the same power to an ulp, without
+    // pow's logarithm and exponential on the slow FP64 pipe
+    return alpha == 1.5 ? x * sqrt(x) : pow(x, alpha);
 }
 
 // Refine one row in place: edges (N+1), hist (N, cleared on return).
