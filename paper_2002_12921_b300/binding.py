@@ -471,6 +471,38 @@ class VegasBatch:
             pass
 
 
+def autotune(dim, nbins, mode, integrand, params, n, adapt=False, blocks=(128, 256),
+             blocks_per_sm=(0, 2, 3), min_samples=(8, 64), reps=3, device="cuda"):
+    """Pick a launch configuration (vegas_set_config) for iterations of n
+    samples of this shape by timing `reps` iterations per candidate on a
+    scratch state (CUDA events, best of reps).  Samples depend only on their
+    counters, so the choice changes speed, never results.  Returns
+    (best config as a dict for Vegas.config, {candidate: ms})."""
+    import itertools
+
+    import torch
+
+    timings = {}
+    for bt, bps, ms in itertools.product(blocks, blocks_per_sm, min_samples):
+        v = Vegas(dim, nbins, 1, mode, integrand, params, max_iters=reps + 1, device=device)
+        try:
+            v.config(block_threads=bt, blocks_per_sm=bps, min_samples_per_thread=ms)
+            v.iterate(n, adapt)  # warm-up
+            best = float("inf")
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(v.stream)
+                v.iterate(n, adapt)
+                e1.record(v.stream)
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            timings[(bt, bps, ms)] = best
+        finally:
+            v.close()
+    bt, bps, ms = min(timings, key=timings.get)
+    return dict(block_threads=bt, blocks_per_sm=bps, min_samples_per_thread=ms), timings
+
+
 def autotune_batch(batch, blocks=(128, 256), tiles=(16384, 32768, 65536, 131072), reps=2,
                    alpha=1.5):
     """Pick (block_threads, tile_samples) for a batch by timing one adapting

@@ -1,6 +1,7 @@
 // Host side of the batch API (include/vegas.h) and its two small kernels:
 // batch_post_kernel refines every (integral, dimension) row and records each
 // integral's estimate; batch_init_kernel resets grids, histograms and logs.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -198,7 +199,10 @@ T* at(const vegas_batch* b, size_t off) {
 }
 
 // Cut every integral's samples into tiles of b->tile_samples (the last one
-// shorter), integral by integral, and copy the table to the device.
+// shorter) and copy the table to the device.  Blocks take tiles in table
+// order, so the table runs from the costliest tiles (samples x dimension) to
+// the cheapest: the last tiles of an iteration, which decide how long the
+// other blocks wait, are then the short ones.
 int build_tiles(vegas_batch* b) {
     b->tiles.clear();
     for (int i = 0; i < b->count; ++i)
@@ -209,6 +213,9 @@ int build_tiles(vegas_batch* b) {
             t.count = (unsigned)((b->n[i] - s) < b->tile_samples ? (b->n[i] - s) : b->tile_samples);
             b->tiles.push_back(t);
         }
+    std::stable_sort(b->tiles.begin(), b->tiles.end(), [b](const BatchTile& x, const BatchTile& y) {
+        return (uint64_t)x.count * b->dims[x.b] > (uint64_t)y.count * b->dims[y.b];
+    });
     if (b->tiles.size() > b->L.max_tiles) return VEGAS_EINVAL;
     b->num_tiles = (unsigned)b->tiles.size();
     return cudaMemcpyAsync(at<BatchTile>(b, b->L.tiles), b->tiles.data(),

@@ -219,6 +219,19 @@ def test_launch_configuration_and_chunking_do_not_change_results():
         assert np.allclose(g["edges"], base["edges"], rtol=1e-13, atol=1e-16)
 
 
+def test_autotuner_picks_a_candidate_that_keeps_results():
+    p = W.gauss_params(6, 0.15)
+    cfg, timings = V.binding.autotune(6, 40, V.VEGAS_FP32_EVAL, W.GAUSS, p, 400_000,
+                                      blocks=(128, 256), blocks_per_sm=(0, 2),
+                                      min_samples=(8,), reps=2)
+    assert len(timings) == 4 and all(t > 0 for t in timings.values())
+    assert (cfg["block_threads"], cfg["blocks_per_sm"], cfg["min_samples_per_thread"]) in timings
+    sched = [(300_007, 1), (300_007, 0)]
+    base = gpu_run(6, 40, 3, W.GAUSS, p, sched, V.VEGAS_FP64)
+    tuned = gpu_run(6, 40, 3, W.GAUSS, p, sched, V.VEGAS_FP64, cfg=cfg)
+    assert rel(tuned["rows"][:, 4], base["rows"][:, 4]) < 1e-13
+
+
 def test_fp64_nonfinite_is_counted_and_reported():
     """A width of 1e-300 makes the Gaussian's prefactor overflow: every f J is
     non-finite, is left out of the sums and vegas_result reports it."""

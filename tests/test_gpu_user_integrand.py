@@ -159,3 +159,28 @@ def test_errors_and_checkpoint(so):
     u.close()
     r.close()
     assert ctypes.sizeof(V.vegas_user_integrand) >= 24
+
+
+@pytest.mark.parametrize("mode", [V.VEGAS_FP64, V.VEGAS_FP32_EVAL])
+def test_nonfinite_user_values_are_counted_and_left_out(so, mode):
+    """NaN where x_1 < 1/4, 1 elsewhere, on the uniform 4-bin grid: the bad
+    samples are those whose first Philox word is below 2^30 (bin 0 of
+    dimension 1), counted here from the oracle's words.  The iteration must
+    report exactly that many non-finite values, the estimate (n - bad)/n, and
+    a histogram holding each finite sample's (f J)^2 = 1 in its bins."""
+    n, seed = 100_003, 21
+    v = user_state(so, "user_hole_d2", 2, 4, seed, mode)
+    v.iterate(n, 1)
+    row, hist = v.iterations()[0], v.histogram()
+    v.close()
+    i = np.arange(n, dtype=np.uint64)
+    ctrs = np.stack([(i & 0xFFFFFFFF).astype(np.uint32), (i >> 32).astype(np.uint32),
+                     np.zeros(n, np.uint32), np.zeros(n, np.uint32)], axis=1)
+    w = oracle.philox(ctrs, np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32))
+    bins = (w[:, :2].astype(np.uint64) * 4) >> 32
+    bad = int(np.sum(bins[:, 0] == 0))
+    assert row[3] == bad
+    assert row[0] == n - bad and row[4] == (n - bad) / n
+    ok = bins[:, 0] != 0
+    for k in range(2):
+        assert np.array_equal(hist[k], np.bincount(bins[ok, k].astype(np.int64), minlength=4))

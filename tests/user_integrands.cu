@@ -44,7 +44,17 @@ struct UserSine {
     }
 };
 
+// NaN where x_1 < 1/4, else 1: on a uniform grid of 4 bins the non-finite
+// samples are exactly those in the first bin of dimension 1.
+struct UserHole {
+    template <typename R, int D>
+    __device__ R operator()(const R (&x)[D], const void*) const {
+        return x[0] < (R)0.25 ? (R)NAN : (R)1;
+    }
+};
+
 VEGAS_USER_INTEGRAND(user_gauss_d4, UserGauss, 4)
+VEGAS_USER_INTEGRAND(user_hole_d2, UserHole, 2)
 VEGAS_USER_INTEGRAND(user_gauss_d8, UserGauss, 8)
 VEGAS_USER_INTEGRAND(user_sum_square_d5, UserSumSquare, 5)
 VEGAS_USER_INTEGRAND(user_sine_d3, UserSine, 3)
