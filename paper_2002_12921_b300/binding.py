@@ -503,7 +503,7 @@ def autotune(dim, nbins, mode, integrand, params, n, adapt=False, blocks=(128, 2
     return dict(block_threads=bt, blocks_per_sm=bps, min_samples_per_thread=ms), timings
 
 
-def autotune_batch(batch, blocks=(128, 256), tiles=(16384, 32768, 65536, 131072), reps=2,
+def autotune_batch(batch, blocks=(128, 256), tiles=(8192, 16384, 32768, 65536, 131072), reps=2,
                    alpha=1.5):
     """Pick (block_threads, tile_samples) for a batch by timing one adapting
     iteration of every integral per candidate (CUDA events on the batch's
