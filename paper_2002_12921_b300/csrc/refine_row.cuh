@@ -60,17 +60,20 @@ __device__ __forceinline__ void refine_row(double* edges, double* hist, int N, d
     const bool refine = N >= 2 && total > 0.0 && total <= DBL_MAX;
 
     if (refine) {
+        // (multiplications by 1/3 and by 1/sum instead of divisions: the same
+        // values to an ulp, with fewer instructions on the slow FP64 pipe)
+        constexpr double kThird = 1.0 / 3.0;
         double ps = 0.0;
         for (int j = threadIdx.x; j < N; j += blockDim.x) {
             double s;
-            if (j == 0) s = (h[0] + h[1]) / 2.0;
-            else if (j == N - 1) s = (h[N - 2] + h[N - 1]) / 2.0;
-            else s = (h[j - 1] + h[j] + h[j + 1]) / 3.0;
+            if (j == 0) s = (h[0] + h[1]) * 0.5;
+            else if (j == N - 1) s = (h[N - 2] + h[N - 1]) * 0.5;
+            else s = (h[j - 1] + h[j] + h[j + 1]) * kThird;
             m[j] = s;
             ps += s;
         }
-        const double ssum = block_sum_all(ps, sbuf);
-        for (int j = threadIdx.x; j < N; j += blockDim.x) m[j] = damp(m[j] / ssum, alpha);
+        const double inv_ssum = 1.0 / block_sum_all(ps, sbuf);
+        for (int j = threadIdx.x; j < N; j += blockDim.x) m[j] = damp(m[j] * inv_ssum, alpha);
         __syncthreads();
 
         // inclusive scan of m into C[1..N] by warp 0, 32 bins at a time

@@ -243,6 +243,48 @@ def test_fp64_nonfinite_is_counted_and_reported():
     assert g["result"][4] is True
 
 
+@pytest.mark.parametrize("mode", [V.VEGAS_FP64, V.VEGAS_FP32_EVAL])
+def test_full_size_d8_workload_one_step_parity(mode):
+    """The d=8 Gaussian workload at full size (10 adapting iterations of 1e7,
+    then 5 fixed-grid iterations of 1e8) in the default launch configuration,
+    the one bench.py times.  For sampled iterations the oracle recomputes the
+    iteration on the grid the GPU used (same counters), and the refinement from
+    the GPU's own histogram; each comparison is then one step, with the FP64
+    bound 1e-12 or the float budget 1e-5 (d=8)."""
+    import os
+
+    wl = W.c2_gauss8()
+    v = V.Vegas(wl.dim, wl.nbins, wl.seed, mode, wl.integrand, wl.params, max_iters=16)
+    grids, hists = [], {}
+    check = [0, 4, 9, 10, 14]
+    for t, (n, adapt) in enumerate(wl.schedule):
+        grids.append(v.grid())
+        v.iterate(n, adapt)
+        if adapt:
+            if t in check:
+                hists[t] = v.histogram()
+            v.refine(1.5)
+    grids.append(v.grid())
+    rows = v.iterations()
+    v.close()
+    tol = RTOL64 if mode == V.VEGAS_FP64 else 1e-5
+    nt = os.cpu_count() or 1
+    for t in check:
+        n, adapt = wl.schedule[t]
+        o = oracle.iterate(grids[t], wl.seed, t, n, wl.integrand, wl.params, adapt, nthreads=nt)
+        assert rows[t][2] == n and rows[t][3] == o["nonfinite"] == 0
+        assert rel(rows[t][4], o["I"]) < tol, (t, rows[t][4], o["I"])
+        assert abs(rows[t][5] - o["var"]) <= 10 * tol * (o["var"] + o["I"] ** 2 / n), t
+        if adapt:
+            if mode == V.VEGAS_FP64:
+                assert np.allclose(hists[t], o["hist"], rtol=1e-11, atol=0), t
+            else:
+                assert np.allclose(hists[t].sum(axis=1), o["hist"].sum(axis=1), rtol=10 * tol)
+            # the refinement of the GPU's histogram: FP64 on both sides
+            assert np.allclose(grids[t + 1], oracle.refine(grids[t], hists[t], 1.5),
+                               rtol=RTOL64, atol=1e-15), t
+
+
 # ---------------------------------------------------------------- FP32-eval mode
 @pytest.mark.parametrize("fid,dim,nbins,tol", [(W.GAUSS, 4, 50, 1e-5), (W.GAUSS, 8, 50, 1e-5),
                                                (W.GAUSS_MIX2, 16, 100, 3e-5),
