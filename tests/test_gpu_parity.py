@@ -285,6 +285,62 @@ def test_full_size_d8_workload_one_step_parity(mode):
                                rtol=RTOL64, atol=1e-15), t
 
 
+def _range_sums(mode, wl, grid, t, begin, end):
+    """{S1, S2, nonfinite} of samples [begin, end) of iteration t of wl on
+    `grid`, from a state advanced to iteration t (vegas_iterate_range)."""
+    from paper_2002_12921_b300.shard import GpuShardEngine
+
+    v = V.Vegas(wl.dim, wl.nbins, wl.seed, mode, wl.integrand, wl.params, max_iters=t + 2)
+    v.set_grid(grid)
+    # fixed-grid iterations move the iteration counter to t; on this grid their
+    # estimate also sets the float path's pre-scale close to the real one
+    for _ in range(t):
+        v.iterate(1_000_000, 0)
+    eng = GpuShardEngine(v)
+    eng.iterate_range(wl.schedule[t][0], begin, end, False)
+    out = eng.export()[:3].cpu().numpy().copy()
+    v.close()
+    return out
+
+
+@pytest.mark.parametrize("mode", [V.VEGAS_FP64, V.VEGAS_FP32_EVAL])
+def test_full_size_d16_mixture_sampled_parity(mode):
+    """The d=16 mixture at full size (iterations of 1e9 samples in 1e8-sample
+    launches, as bench.py runs it): on the grid of the third iteration, two
+    sampled index ranges, one in the middle (across a launch boundary) and one
+    ending at the last sample, reproduce the oracle's partial sums over the
+    same indices; and
+    (FP64) the ten 1e8-sample chunks' sums add up to the full iteration's sum."""
+    import os
+
+    wl = W.c5_mix16()
+    n, t = wl.schedule[0][0], 2
+    v = V.Vegas(wl.dim, wl.nbins, wl.seed, mode, wl.integrand, wl.params, max_iters=8)
+    v.config(chunk_samples=wl.chunk)
+    grids = []
+    for _ in range(t + 1):
+        grids.append(v.grid())
+        v.iterate(n, 1)
+        v.refine(1.5)
+    rows = v.iterations()
+    v.close()
+    assert rows[t][2] == n
+    tol = RTOL64 if mode == V.VEGAS_FP64 else 3e-5
+    nt = os.cpu_count() or 1
+    for begin in (n // 2 - 1_000_000, n - 2_000_000):
+        end = begin + 2_000_000
+        got = _range_sums(mode, wl, grids[t], t, begin, end)
+        o = oracle.iterate_range(grids[t], wl.seed, t, begin, end - begin, wl.integrand,
+                                 wl.params, False, nthreads=nt)
+        assert got[2] == o["nonfinite"] == 0
+        assert rel(got[0], o["S1"]) < tol, (begin, got[0], o["S1"])
+        assert rel(got[1], o["S2"]) < 2 * tol, (begin, got[1], o["S2"])
+    if mode == V.VEGAS_FP64:
+        parts = [_range_sums(mode, wl, grids[t], t, c, c + wl.chunk)[0]
+                 for c in range(0, n, wl.chunk)]
+        assert rel(sum(parts), rows[t][0]) < 1e-13
+
+
 # ---------------------------------------------------------------- FP32-eval mode
 @pytest.mark.parametrize("fid,dim,nbins,tol", [(W.GAUSS, 4, 50, 1e-5), (W.GAUSS, 8, 50, 1e-5),
                                                (W.GAUSS_MIX2, 16, 100, 3e-5),
