@@ -53,7 +53,8 @@ extern "C" {
 #define VEGAS_EINVAL 1     /* an argument is out of range or NULL */
 #define VEGAS_ECUDA 2      /* a CUDA runtime call failed (launch or sync) */
 #define VEGAS_ENONFINITE 3 /* some f*J was NaN or infinite (left out of the sums) */
-#define VEGAS_ESTATE 4     /* call out of order, iteration log full, bad grid */
+#define VEGAS_ESTATE 4     /* call out of order, iteration log full, bad grid, or (debug
+                              build) a failed device check */
 #define VEGAS_ENOSPACE 5   /* workspace smaller than vegas_workspace_bytes() */
 
 /* ---- precision modes ---------------------------------------------------- */
@@ -85,6 +86,14 @@ extern "C" {
  *                  attached with vegas_set_user_integrand before the first
  *                  iteration; params ignored. */
 #define VEGAS_USER 5
+
+/* ---- debug build ---------------------------------------------------------- */
+/* libvegas_b300_debug.so (the same sources built with VEGAS_DEBUG_CHECKS) adds
+ * device checks to the iterate kernels: every block checks the state's grid
+ * (per dimension 0 and 1 at the ends, finite, strictly increasing edges) and
+ * every sample its bin index (< nbins) and mapped coordinate (finite).  A failed check sets a
+ * bit of the state's device status word; vegas_result, vegas_get_iterations
+ * and the batch result calls then return VEGAS_ESTATE.  Nothing traps. */
 
 /* ---- limits --------------------------------------------------------------- */
 #define VEGAS_MAX_DIM 20
@@ -310,7 +319,8 @@ int vegas_iterate_noalloc(double *d_edges, int dim, int nbins, uint64_t seed, ui
  * would have.  Export synchronises the stream.  With buf == NULL, *bytes
  * receives the blob size; otherwise *bytes must hold at least that size. */
 int vegas_export_state(vegas_state *s, void *buf, size_t *bytes);
-/* Create a state from a blob (VEGAS_EINVAL if it is malformed or of another
+/* Create a state from a blob (VEGAS_EINVAL if it is malformed -- including a
+ * grid vegas_set_grid would refuse -- or of another
  * format version) on a caller workspace of at least vegas_workspace_bytes()
  * for the blob's shape and iteration capacity.  Asynchronous on the stream. */
 int vegas_import_state(vegas_state **out, const void *buf, size_t bytes, void *d_workspace,

@@ -10,7 +10,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libvegas_b300.so")
+# the library this binding loads: the release build, or another build of the
+# same sources (e.g. the debug build) named by VEGAS_B300_LIBRARY
+LIB_PATH = os.environ.get("VEGAS_B300_LIBRARY") or os.path.join(HERE, "_build", "libvegas_b300.so")
 
 VEGAS_OK, VEGAS_EINVAL, VEGAS_ECUDA, VEGAS_ENONFINITE, VEGAS_ESTATE, VEGAS_ENOSPACE = range(6)
 VEGAS_FP64, VEGAS_FP32_EVAL = 0, 1

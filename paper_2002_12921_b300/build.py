@@ -3,7 +3,8 @@
 Every translation unit under csrc/ is compiled by nvcc for
 ``-gencode arch=compute_103a,code=sm_103a`` (in parallel, one process per
 unit) and linked into ``paper_2002_12921_b300/_build/libvegas_b300.so``.
-Usage: ``python -m paper_2002_12921_b300.build [--force] [--verbose]``.
+Usage: ``python -m paper_2002_12921_b300.build [--force] [--verbose] [--debug]``
+(``--debug``: ``_build/debug/libvegas_b300_debug.so`` with the device checks).
 ``build_user_integrand`` compiles a caller's integrand file the same way.
 """
 import concurrent.futures as cf
@@ -18,6 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "libvegas_b300.so"
 LIB = os.path.join(OUT_DIR, LIB_NAME)
+DEBUG_DIR = os.path.join(OUT_DIR, "debug")
+DEBUG_LIB = os.path.join(DEBUG_DIR, "libvegas_b300_debug.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -48,11 +51,11 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src, verbose):
-    obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+def _compile(src, verbose, out_dir=OUT_DIR, extra=()):
+    obj = os.path.join(out_dir, os.path.basename(src) + ".o")
     if not _stale(obj, [src] + headers()):
         return obj
-    cmd = [nvcc()] + ARCH + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + \
+    cmd = [nvcc()] + ARCH + NVCC_FLAGS + list(extra) + (["-Xptxas", "-v"] if verbose else []) + \
         ["-c", src, "-o", obj + ".tmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -63,24 +66,28 @@ def _compile(src, verbose):
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link the library if any source is newer; return its path."""
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile and link the library if any source is newer; return its path.
+    debug=True builds libvegas_b300_debug.so, the same sources with the device
+    checks of VEGAS_DEBUG_CHECKS (include/vegas.h, "debug build")."""
+    out_dir, lib = (DEBUG_DIR, DEBUG_LIB) if debug else (OUT_DIR, LIB)
+    extra = ("-DVEGAS_DEBUG_CHECKS",) if debug else ()
+    os.makedirs(out_dir, exist_ok=True)
     srcs = sources()
     if force:
-        for o in glob.glob(os.path.join(OUT_DIR, "*.o")):
+        for o in glob.glob(os.path.join(out_dir, "*.o")):
             os.remove(o)
     workers = max(1, min(len(srcs), os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(workers) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
-    if force or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, verbose, out_dir, extra), srcs))
+    if force or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 def build_module(src: str, out: str, force: bool = False, verbose: bool = False) -> str:
@@ -108,4 +115,5 @@ def build_user_integrand(src: str, out: str, force: bool = False, verbose: bool 
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv,
+                debug="--debug" in sys.argv))

@@ -449,6 +449,7 @@ static int batch_rows(vegas_batch* b, std::vector<double>& rows, int* done) {
                         cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
         cudaStreamSynchronize(b->stream) != cudaSuccess)
         return VEGAS_ECUDA;
+    if (ctrl[kStatus] & kStatusCheckFailed) return VEGAS_ESTATE;
     *done = (int)ctrl[kIter];
     return VEGAS_OK;
 }

@@ -71,9 +71,13 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchTile& 
     __syncthreads();
 
     IterateSink<R, D, ADAPT> sink(shist, N, logr);
-    sample_loop<R, D, Integrand<R, VEGAS_GAUSS>>(
+    bool checks_ok = sample_loop<R, D, Integrand<R, VEGAS_GAUSS>>(
         t.start + threadIdx.x, t.start + t.count, blockDim.x, a.iter, t.b << 8, a.rk0, a.rk1,
         fc, N, (R)(sizeof(R) == 4 ? fc.C32 : fc.C), n4, nlast, sgrid, sink);
+#ifdef VEGAS_DEBUG_CHECKS
+    checks_ok &= edges_ok(a.edges + info.edge_off, D, N);
+#endif
+    report_checks(checks_ok, a.ctrl);
 
     const double s1 = sink.acc.block1(reinterpret_cast<FloatFloat*>(sred));
     const double s2 = sink.acc.block2(reinterpret_cast<FloatFloat*>(sred));

@@ -116,6 +116,15 @@ extern "C" int vegas_import_state(vegas_state** out, const void* buf, size_t byt
     std::vector<double> params(np ? np : 1);
     std::memcpy(params.data(), p, 8 * np);
     p += 8 * np;
+    {  // the grid must be one vegas_set_grid accepts: 0 and 1 at the ends, increasing
+        std::vector<double> e(nbins + 1);
+        for (uint64_t k = 0; k < dim; ++k) {
+            std::memcpy(e.data(), p + 8 * k * (nbins + 1), 8 * (nbins + 1));
+            if (e[0] != 0.0 || e[nbins] != 1.0) return VEGAS_EINVAL;
+            for (uint64_t l = 0; l < nbins; ++l)
+                if (!(e[l + 1] > e[l])) return VEGAS_EINVAL;
+        }
+    }
     vegas_state* s = nullptr;
     int rc = vegas_init_grid(&s, (int)dim, (int)nbins, head[8], (int)head[4], (int)head[5],
                              np ? params.data() : nullptr, (int)np, (int)max_iters, d_workspace,

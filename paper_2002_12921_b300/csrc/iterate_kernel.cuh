@@ -364,9 +364,11 @@ __device__ __forceinline__ void stage_grid(const double* __restrict__ edges, int
 // The samples [first, end) with step `stride` of iteration `it`: Philox words
 // (the first two rounds shared by a sample's calls), grid map, and the
 // integrand F in its staged coordinate; each sample's weight f J, the
-// integrand state and the bins go to sink(fw, f, bins).
+// integrand state and the bins go to sink(fw, f, bins).  Returns whether the
+// debug build's per-sample checks held (bin index < N, mapped coordinate
+// finite); always true in the release build.
 template <typename R, int D, typename F, typename Sink>
-__device__ __forceinline__ void sample_loop(unsigned long long first, unsigned long long end,
+__device__ __forceinline__ bool sample_loop(unsigned long long first, unsigned long long end,
                                             unsigned long long stride, unsigned it,
                                             uint32_t c2base, const unsigned (&rk0)[10],
                                             const unsigned (&rk1)[10], const FnConsts& fc,
@@ -380,6 +382,7 @@ __device__ __forceinline__ void sample_loop(unsigned long long first, unsigned l
     const uint32_t t_key = it ^ rk1[0];
     uint32_t cur_hi = (uint32_t)(first >> 32);
     PhiloxCallConst pc[DC];
+    bool checks_ok = true;
 #pragma unroll
     for (int q = 0; q < DC; ++q) pc[q] = philox_call_const(c2base | (uint32_t)q, cur_hi, rk0, rk1);
     constexpr int kUnroll = sample_unroll<R>();
@@ -413,6 +416,9 @@ __device__ __forceinline__ void sample_loop(unsigned long long first, unsigned l
                     const uint32_t l = w[t] * (uint32_t)N;
                     const Pair g = sgrid[k * N + j];
                     const R x = P::fma(P::unit(l), g.y, g.x);
+#ifdef VEGAS_DEBUG_CHECKS
+                    checks_ok &= j < (uint32_t)N && P::finite(x);
+#endif
                     J *= g.y;
                     f.add(k, x, fc);
                     if (Sink::kNeedBins) bins[k] = j;
@@ -422,6 +428,34 @@ __device__ __forceinline__ void sample_loop(unsigned long long first, unsigned l
         }
         sink(f.value(fc) * J, f, bins);
     }
+    return checks_ok;
+}
+
+// Debug build: whether the grid the block runs on is well formed (per row of
+// N + 1 edges: 0 and 1 at the ends, finite, strictly increasing).  It reads
+// the edges themselves, so a grid corrupted in memory is seen whichever way
+// the block staged it.
+__device__ __forceinline__ bool edges_ok(const double* edges, int D, int N) {
+    bool ok = true;
+    for (int i = threadIdx.x; i < D * N; i += blockDim.x) {
+        const int k = i / N, j = i - k * N;
+        const double* e = edges + (size_t)k * (N + 1) + j;
+        ok &= e[1] > e[0] && e[1] <= DBL_MAX;
+        if (j == 0) ok &= e[0] == 0.0;
+        if (j == N - 1) ok &= e[1] == 1.0;
+    }
+    return ok;
+}
+
+// Debug build: record a failed check in the state's status word (one atomic
+// per block).  A barrier: every thread of the block calls it.
+__device__ __forceinline__ void report_checks(bool ok, unsigned* ctrl) {
+#ifdef VEGAS_DEBUG_CHECKS
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(&ctrl[kStatus], kStatusCheckFailed);
+#else
+    (void)ok;
+    (void)ctrl;
+#endif
 }
 
 // The iterate kernels' sink: per-thread sums of f J and (f J)^2, the count of
@@ -524,10 +558,14 @@ __device__ __forceinline__ void iterate_body(const IterArgs& a) {
     __syncthreads();
 
     IterateSink<R, D, ADAPT> sink(shist, N, logr);
-    sample_loop<R, D, F>(
+    bool checks_ok = sample_loop<R, D, F>(
         a.i0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x, a.i0 + a.n_chunk,
         (unsigned long long)gridDim.x * blockDim.x, it, a.integral_id << 8, a.rk0, a.rk1, a.fc,
         N, (R)j0, n4, nlast, sgrid, sink);
+#ifdef VEGAS_DEBUG_CHECKS
+    checks_ok &= edges_ok(a.edges, D, N);
+#endif
+    report_checks(checks_ok, a.ctrl);
     const Acc<R>& acc = sink.acc;
     const unsigned bad = sink.bad;
 

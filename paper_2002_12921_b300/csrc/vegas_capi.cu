@@ -518,7 +518,7 @@ static int read_log(vegas_state* s, double* rows, int max_rows, int* n_rows, int
         cudaSuccess)
         return VEGAS_ECUDA;
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return VEGAS_ECUDA;
-    if (ctrl[kStatus] & kStatusLogFull) return VEGAS_ESTATE;
+    if (ctrl[kStatus] & (kStatusLogFull | kStatusCheckFailed)) return VEGAS_ESTATE;
     int n = (int)ctrl[kIter];
     if (n > max_rows) n = max_rows;
     if (n > 0) {

@@ -49,7 +49,10 @@ constexpr int kNumIntegrands = 5;
 // control words in device memory
 enum CtrlWord { kTicket = 0, kIter = 1, kStatus = 2, kCtrlWords = 64 };
 // status bits
-enum StatusBit { kStatusLogFull = 1u };
+// kStatusCheckFailed: a debug build's device check failed (a staged grid bin
+// with a non-finite coordinate or a width that is not positive -- edges not
+// increasing --, a bin index out of range, a non-finite mapped coordinate).
+enum StatusBit { kStatusLogFull = 1u, kStatusCheckFailed = 2u };
 
 // Integrand constants, precomputed on the host from the user's parameters.
 //

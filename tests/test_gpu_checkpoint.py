@@ -40,3 +40,22 @@ def test_resume_equals_uninterrupted_run(mode):
     assert len(b.export_state()) == len(a.export_state())
     a.close()
     b.close()
+
+
+def test_import_refuses_a_blob_whose_grid_is_not_increasing():
+    """A blob is checked like vegas_set_grid's input: swapping two edges of one
+    dimension makes the import fail with VEGAS_EINVAL."""
+    import struct
+
+    p = W.gauss_params(3, 0.2)
+    a = V.Vegas(3, 10, 5, V.VEGAS_FP64, W.GAUSS, p, max_iters=4)
+    a.run([(50_000, 1)] * 2)
+    blob = bytearray(a.export_state())
+    a.close()
+    (nparams,) = struct.unpack_from("<Q", blob, 7 * 8)
+    off = 16 * 8 + 8 * nparams + 8 * (11 + 4)  # dimension 1, edges 4 and 5
+    e4, e5 = struct.unpack_from("<dd", blob, off)
+    struct.pack_into("<dd", blob, off, e5, e4)
+    with pytest.raises(V.VegasError) as exc:
+        V.Vegas.from_state(bytes(blob))
+    assert exc.value.status == V.VEGAS_EINVAL
