@@ -165,6 +165,13 @@ int vegas_result(vegas_state *s, int first_iter, double *mean, double *sigma, do
  * t < min(max_rows, n_iter).  Synchronises the stream. */
 int vegas_get_iterations(vegas_state *s, double *host_rows, int max_rows, int *n_rows);
 
+/* Device time of each logged iteration, in ns of the GPU's global timer: from
+ * the start of the first block of its first launch to the end of its last
+ * launch's reduction (launch gaps inside a chunked iteration included, launch
+ * latency before it not); for a sharded iteration, this rank's own range.
+ * host_ns: max_rows doubles; *n_rows receives the count.  Synchronises. */
+int vegas_get_iteration_times(vegas_state *s, double *host_ns, int max_rows, int *n_rows);
+
 /* Copy the grid (dim x (nbins+1) doubles, row-major) to / from host memory.
  * vegas_set_grid checks e_0 = 0, e_N = 1 and strict increase (VEGAS_ESTATE
  * otherwise).  Both synchronise the stream. */

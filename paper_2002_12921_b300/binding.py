@@ -31,7 +31,7 @@ EXPORTED = ("vegas_workspace_bytes", "vegas_init_grid", "vegas_set_config", "veg
             "vegas_batch_result", "vegas_batch_get_log", "vegas_batch_get_grid",
             "vegas_batch_destroy", "vegas_iterate_range", "vegas_shard_export",
             "vegas_shard_import", "vegas_export_state", "vegas_import_state",
-            "vegas_set_user_integrand")
+            "vegas_set_user_integrand", "vegas_get_iteration_times")
 
 
 class VegasError(RuntimeError):
@@ -68,6 +68,7 @@ def lib():
         L.vegas_refine.argtypes = [vp, dbl]
         L.vegas_result.argtypes = [vp, i32, dp, dp, dp, ip]
         L.vegas_get_iterations.argtypes = [vp, vp, i32, ip]
+        L.vegas_get_iteration_times.argtypes = [vp, vp, i32, ip]
         L.vegas_get_grid.argtypes = [vp, vp]
         L.vegas_set_grid.argtypes = [vp, vp]
         L.vegas_get_histogram.argtypes = [vp, vp]
@@ -161,6 +162,15 @@ def vegas_get_iterations(h, max_rows=1 << 16):
     _check(lib().vegas_get_iterations(h, rows.ctypes.data, max_rows, ctypes.byref(n)),
            "vegas_get_iterations")
     return rows[: n.value].copy()
+
+
+def vegas_get_iteration_times(h, max_rows=1 << 16):
+    """Device time of each logged iteration in ns (numpy array)."""
+    t = np.zeros(max_rows)
+    n = ctypes.c_int()
+    _check(lib().vegas_get_iteration_times(h, t.ctypes.data, max_rows, ctypes.byref(n)),
+           "vegas_get_iteration_times")
+    return t[: n.value].copy()
 
 
 def vegas_get_grid(h, dim, nbins):
@@ -313,6 +323,10 @@ class Vegas:
 
     def iterations(self):
         return vegas_get_iterations(self.handle)
+
+    def iteration_times(self):
+        """Device time of each logged iteration, ns."""
+        return vegas_get_iteration_times(self.handle)
 
     def grid(self):
         return vegas_get_grid(self.handle, self.dim, self.nbins)

@@ -513,6 +513,13 @@ __device__ __forceinline__ void jacobian_factors(int N, R& n4, R& nlast) {
     nlast = (R)nrem;
 }
 
+// The GPU's global nanosecond timer.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // ------------------------------------------------------------------------
 // The kernel body.  R = float or double, D = dimension, F = integrand type,
 // ADAPT = accumulate the refinement histogram.
@@ -538,6 +545,9 @@ __device__ __forceinline__ void iterate_body(const IterArgs& a) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctrl[kStatus], kStatusLogFull);
         return;
     }
+    // this block's start time, published after the samples (below)
+    __shared__ unsigned long long s_start;
+    if (threadIdx.x == 0) s_start = global_ns();
     stage_grid<R, D, ADAPT>(a.edges, N, logr, a.fc, sgrid, shist, a.staged32);
 
     // Pre-scale of the float path: f J is carried as f J 2^-h with 2^h near the
@@ -581,7 +591,11 @@ __device__ __forceinline__ void iterate_body(const IterArgs& a) {
 
     // Publish the block partial; the last block to finish reduces them all in
     // block order and appends the iteration to the log.
+    // the iteration's start: the earliest block start of its first launch, kept
+    // as a maximum of complements so that 0 means "not started"
+    unsigned long long* t0c = reinterpret_cast<unsigned long long*>(a.ctrl + kT0);
     if (threadIdx.x == 0) {
+        if (a.first_chunk) atomicMax(t0c, ~s_start);
         double* p = a.partials + (size_t)blockIdx.x * kPartialStride;
         p[0] = b1 * sc1;
         p[1] = b2 * sc2;
@@ -617,8 +631,11 @@ __device__ __forceinline__ void iterate_body(const IterArgs& a) {
             const double var = (L[1] / n - I * I) / (n - 1.0);
             L[4] = I;
             L[5] = var > 0.0 ? var : 0.0;
-            L[6] = 0.0;
+            // device time of the iteration: first block start to this point
+            const unsigned long long c = *reinterpret_cast<volatile unsigned long long*>(t0c);
+            L[6] = c ? (double)(global_ns() - ~c) : 0.0;
             L[7] = 0.0;
+            *t0c = 0ull;
             a.ctrl[kIter] = it + 1;
         }
         a.ctrl[kTicket] = 0u;

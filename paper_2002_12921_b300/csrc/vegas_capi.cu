@@ -575,6 +575,22 @@ int vegas_get_iterations(vegas_state* s, double* host_rows, int max_rows, int* n
     return rc;
 }
 
+int vegas_get_iteration_times(vegas_state* s, double* host_ns, int max_rows, int* n_rows) {
+    if (!s || !host_ns || max_rows < 0 || !n_rows) return VEGAS_EINVAL;
+    DeviceGuard g(s->device);
+    if (!g.ok) return VEGAS_ECUDA;
+    double* rows = new (std::nothrow) double[(size_t)s->max_iters * kLogStride];
+    if (!rows) return VEGAS_EINVAL;
+    int n = 0;
+    const int rc = read_log(s, rows, max_rows < s->max_iters ? max_rows : s->max_iters, &n,
+                            nullptr, 0);
+    if (rc == VEGAS_OK)
+        for (int t = 0; t < n; ++t) host_ns[t] = rows[(size_t)t * kLogStride + 6];
+    *n_rows = rc == VEGAS_OK ? n : 0;
+    delete[] rows;
+    return rc;
+}
+
 int vegas_get_grid(vegas_state* s, double* host_edges) {
     if (!s || !host_edges) return VEGAS_EINVAL;
     DeviceGuard g(s->device);

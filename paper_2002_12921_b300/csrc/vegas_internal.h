@@ -47,7 +47,9 @@ constexpr int kLogStride = 8;       // doubles per log row: S1, S2, n, nonfinite
 constexpr int kNumIntegrands = 5;
 
 // control words in device memory
-enum CtrlWord { kTicket = 0, kIter = 1, kStatus = 2, kCtrlWords = 64 };
+// kT0: words 4-5, the complement of the %globaltimer value (ns) at which the
+// current iteration's first block started (0: none yet).
+enum CtrlWord { kTicket = 0, kIter = 1, kStatus = 2, kT0 = 4, kCtrlWords = 64 };
 // status bits
 // kStatusCheckFailed: a debug build's device check failed (a staged grid bin
 // with a non-finite coordinate or a width that is not positive -- edges not

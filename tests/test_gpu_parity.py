@@ -232,6 +232,33 @@ def test_autotuner_picks_a_candidate_that_keeps_results():
     assert rel(tuned["rows"][:, 4], base["rows"][:, 4]) < 1e-13
 
 
+def test_iteration_device_times_match_cuda_events():
+    """vegas_get_iteration_times: each iteration's device time is positive, no
+    longer than the CUDA-event time around its launches and most of it; a
+    chunked iteration is timed across its launches."""
+    p = W.gauss_params(8, 0.1)
+    v = V.Vegas(8, 50, 2, V.VEGAS_FP32_EVAL, W.GAUSS, p, max_iters=8)
+    s = torch.cuda.current_stream()
+    v.iterate(10_000_000, 1)  # warm-up
+    v.refine(1.5)
+    events = []
+    for n, cfg in [(10_000_000, {}), (100_000_000, {}), (100_000_000, {"chunk_samples": 25_000_000})]:
+        if cfg:
+            v.config(**cfg)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        v.iterate(n, 0)
+        e1.record(s)
+        events.append((e0, e1))
+    torch.cuda.synchronize()
+    t_dev = v.iteration_times() * 1e-6  # ms
+    v.close()
+    assert len(t_dev) == 4 and np.all(t_dev > 0)
+    for (e0, e1), td in zip(events, t_dev[1:]):
+        te = e0.elapsed_time(e1)
+        assert 0.5 * te <= td <= te * 1.02 + 0.005, (td, te)
+
+
 def test_fp64_nonfinite_is_counted_and_reported():
     """A width of 1e-300 makes the Gaussian's prefactor overflow: every f J is
     non-finite, is left out of the sums and vegas_result reports it."""
