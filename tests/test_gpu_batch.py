@@ -21,10 +21,11 @@ def _cuda():
 
 
 def small_batch():
-    """Five Gaussians of uneven dimension and sample count."""
+    """Six Gaussians of uneven dimension (up to the maximum, 20) and sample
+    count."""
     rng = np.random.Generator(np.random.PCG64(11))
-    dims = [2, 5, 8, 13, 16]
-    ns = [3000, 20011, 12345, 7777, 40000]
+    dims = [2, 5, 8, 13, 16, 20]
+    ns = [3000, 20011, 12345, 7777, 40000, 15001]
     params = [W.gauss_params(d, float(rng.uniform(0.1, 0.3)), rng.uniform(0.3, 0.7, d))
               for d in dims]
     return dims, ns, params
@@ -70,7 +71,8 @@ def test_tile_size_and_block_size_do_not_change_results():
         B = V.VegasBatch(dims, ns, 30, 9, V.VEGAS_FP64, params, max_iters=4)
         B.config(block_threads=bt, tile_samples=ts)
         B.run(3)
-        runs.append((B.log()[:, :3, 4], np.concatenate([B.grid(b).ravel() for b in range(5)])))
+        grids = np.concatenate([B.grid(b).ravel() for b in range(len(dims))])
+        runs.append((B.log()[:, :3, 4], grids))
         B.close()
     for I, e in runs[1:]:
         assert np.allclose(I, runs[0][0], rtol=1e-12, atol=0)
@@ -83,7 +85,7 @@ def test_batch_fp32_close_to_fp64():
     for mode in (V.VEGAS_FP64, V.VEGAS_FP32_EVAL):
         B = V.VegasBatch(dims, ns, 30, 5, mode, params, max_iters=4)
         B.run(4)
-        out[mode] = [B.result(b, 1) for b in range(5)]
+        out[mode] = [B.result(b, 1) for b in range(len(dims))]
         B.close()
     for r64, r32 in zip(out[V.VEGAS_FP64], out[V.VEGAS_FP32_EVAL]):
         assert abs(r32[0] - r64[0]) < 0.05 * r64[1]

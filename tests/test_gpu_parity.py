@@ -180,7 +180,8 @@ def test_fp64_gauss_d8_adapt_then_fixed():
                                            (W.GAUSS, 1, 2), (W.GAUSS, 16, 100),
                                            (W.GAUSS, 2, 1024), (W.GAUSS, 8, 1),
                                            (W.GAUSS, 20, 50), (W.GAUSS_MIX2, 20, 40),
-                                           (W.GENZ_DISC, 17, 20), (W.GENZ_PPEAK, 19, 30)])
+                                           (W.GENZ_DISC, 17, 20), (W.GENZ_PPEAK, 19, 30),
+                                           (W.GAUSS, 8, 1024), (W.GAUSS, 20, 409)])
 def test_fp64_integrands_and_shapes(fid, dim, nbins):
     if fid in (W.GAUSS, ):
         p = W.gauss_params(dim, 0.2, np.linspace(0.3, 0.7, dim))
@@ -204,6 +205,17 @@ def test_fp64_tiny_and_ragged_n(n):
     o = oracle.run(3, 10, 5, W.GAUSS, p, sched)
     g = gpu_run(3, 10, 5, W.GAUSS, p, sched, V.VEGAS_FP64)
     assert_fp64_parity(g, o, sched)
+
+
+def test_fewer_than_two_samples_are_refused():
+    v = V.Vegas(3, 10, 1, V.VEGAS_FP64, W.GAUSS, W.gauss_params(3, 0.2), max_iters=4)
+    for n in (0, 1):
+        with pytest.raises(V.VegasError) as e:
+            v.iterate(n, 1)
+        assert e.value.status == V.VEGAS_EINVAL
+    v.iterate(2, 1)
+    assert v.iterations().shape[0] == 1
+    v.close()
 
 
 def test_launch_configuration_and_chunking_do_not_change_results():
@@ -373,7 +385,8 @@ def test_full_size_d16_mixture_sampled_parity(mode):
                                                (W.GAUSS_MIX2, 16, 100, 3e-5),
                                                (W.GENZ_PPEAK, 6, 30, 1e-5),
                                                (W.GENZ_DISC, 5, 30, 1e-5), (W.FLAT, 3, 11, 1e-6),
-                                               (W.GAUSS, 20, 50, 4e-5)])
+                                               (W.GAUSS, 20, 50, 4e-5),
+                                               (W.GAUSS, 8, 1024, 1e-5)])
 def test_fp32_single_iteration_against_fp64_oracle(fid, dim, nbins, tol):
     """Same grid and counters: the float path's I and var are within the float
     error budget of the FP64 oracle's."""
