@@ -570,7 +570,12 @@ def main():
                 "traffic": ITERATE_TRAFFIC_BYTES,
                 "kernel": "vegas_iterate_kernel<float,8,GAUSS,fixed>",
                 "kernel_ms": fixed_ms, "ops_per_sample": alg_ops_per_sample(DIM),
-                "peak_basis": "148 SMs x 128 lanes x 2032 MHz (recipe unit counts and max clock)"}
+                "peak_basis": "148 SMs x 128 lanes x 2032 MHz (recipe unit counts and max clock)",
+                # the unit that binds inside that envelope, from the committed ncu summary
+                "binding_pipe": {"pipe": "fmaheavy: integer multiplies (34 Philox + 8 bin "
+                                         "32x32->64 products per d=8 sample)",
+                                 "busy_ncu": 0.735,
+                                 "summary": "profiles/vegas_kernels_d8_gauss_batch256_adjoint.md"}}
     if clk.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved / (SMS * LANES_PER_SM * clk["sm_mhz"] * 1e6
                                                          / 1e12)
