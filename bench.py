@@ -205,7 +205,9 @@ def run_step_sharded(V, stream, mode, seed, world, fixed_events=None):
     return v
 
 
-LAUNCHES_PER_STEP = 1 + IT_ADAPT * 2 + IT_FIXED  # init, iterate+refine, fixed iterate
+# one FP32 step: init + staging of the float grid, iterate + refine per adapting
+# iteration, iterate per fixed-grid iteration
+LAUNCHES_PER_STEP = 2 + IT_ADAPT * 2 + IT_FIXED
 
 
 def time_mode(V, mode, steps, warmup, seed0, ws, flush, stream, world=1):
