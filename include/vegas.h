@@ -34,9 +34,14 @@
  * Bin and position.  For word w: bin j = floor(w N / 2^32) (exact integer),
  * position l = (w N) mod 2^32.  FP64 mode: frac = (l + 1/2) 2^-32.  FP32 mode:
  * frac = (floor(l / 2^9) + 1/2) 2^-23.  x = e_j + frac (e_{j+1} - e_j),
- * J = prod_k N (e_{j+1} - e_j).  In FP32 mode e_j, e_{j+1} are first rounded to
- * float and their difference is taken in float, so the map stays an exact
- * change of variables of the rounded grid.
+ * J = prod_k N (e_{j+1} - e_j).  In FP32 mode each bin's (start, width) pair --
+ * already in the integrand's own coordinate -- is computed in double and
+ * rounded once to float, and J uses the rounded width: inside every bin the map
+ * is an exact change of variables (adjacent bins may overlap or leave a gap of
+ * an ulp).
+ *
+ * Threads.  A state (or batch) is not thread-safe: calls on one state must not
+ * run concurrently; different states may be used from different host threads.
  */
 #ifndef VEGAS_B300_VEGAS_H
 #define VEGAS_B300_VEGAS_H
