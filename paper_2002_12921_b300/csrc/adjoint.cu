@@ -34,7 +34,7 @@ struct GaussCoords {
     }
     __device__ __forceinline__ R value(const FnConsts&) const {
         if (sizeof(R) == 4) return ex2_approx(-(float)s);
-        return exp(-(double)s);
+        return fp64_exp(-(double)s);
     }
 };
 

@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fp64_exp.cuh"
 #include "philox.cuh"
 #include "stage.cuh"
 #include "vegas_internal.h"
@@ -127,7 +128,7 @@ struct Integrand<double, VEGAS_GAUSS> {
     double s;
     __device__ __forceinline__ void begin() { s = 0.0; }
     __device__ __forceinline__ void add(int, double z, const FnConsts&) { s = fma(z, z, s); }
-    __device__ __forceinline__ double value(const FnConsts&) const { return exp(-s); }
+    __device__ __forceinline__ double value(const FnConsts&) const { return fp64_exp(-s); }
 };
 
 template <>
@@ -140,7 +141,7 @@ struct Integrand<double, VEGAS_GAUSS_MIX2> {
         sb = fma(zb, zb, sb);
     }
     __device__ __forceinline__ double value(const FnConsts&) const {
-        return exp(-sa) + exp(-sb);
+        return fp64_exp(-sa) + fp64_exp(-sb);
     }
 };
 
@@ -162,7 +163,7 @@ struct Integrand<double, VEGAS_GENZ_DISC> {
         inside = inside && (z > c.t64[k]);
     }
     __device__ __forceinline__ double value(const FnConsts&) const {
-        return inside ? exp(s) : 0.0;
+        return inside ? fp64_exp(s) : 0.0;
     }
 };
 

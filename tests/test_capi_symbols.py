@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2002_12921_b300 as V
@@ -91,3 +92,18 @@ def test_user_integrand_descriptors_load_without_a_device(lib):
         sizes.add(desc.args_bytes)
     assert len(sizes) == 1 and sizes.pop() > 0
     assert lib.vegas_set_user_integrand(None, addr, None) == V.VEGAS_EINVAL
+
+
+def test_fp64_exp_table_is_correctly_rounded_powers_of_two():
+    """The 64-entry table of the FP64 path's exponential holds 2^(j/64) rounded
+    to the nearest double (checked against 200-bit arithmetic)."""
+    import mpmath
+
+    mpmath.mp.prec = 200
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_2002_12921_b300", "csrc", "exp2_table.h")
+    vals = [float.fromhex(h) for h in re.findall(r"0x[0-9a-f.]+p[+-]\d+", open(path).read())]
+    assert len(vals) == 64
+    for j, v in enumerate(vals):
+        exact = mpmath.mpf(2) ** (mpmath.mpf(j) / 64)
+        assert abs(mpmath.mpf(v) - exact) <= mpmath.mpf(np.spacing(v)) / 2, j

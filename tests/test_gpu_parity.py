@@ -151,6 +151,46 @@ def test_philox_words_equal_curand_philox4_32_10():
             assert torch.equal(ours[:, 4 * q:4 * q + 4], ref), (seed, q)
 
 
+def test_fp64_exp_within_two_ulp_of_exp_everywhere():
+    """The FP64 integrands' table-driven exponential against the CUDA library's
+    exp and numpy's on the whole argument range, including the subnormal
+    results, the overflow and underflow thresholds and special values."""
+    import ctypes
+    import os
+
+    from paper_2002_12921_b300 import build
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    so = build.build_module(os.path.join(root, "tests", "fp64_exp_check.cu"),
+                            os.path.join(root, "tests", "_build", "libfp64_exp_check.so"))
+    m = ctypes.CDLL(so)
+    m.fp64_exp_eval.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_uint64, ctypes.c_void_p]
+    rng = np.random.Generator(np.random.PCG64(8))
+    kmax, kmin = float.fromhex("0x1.62e42fefa39efp+9"), float.fromhex("-0x1.74910d52d3052p+9")
+    x = np.concatenate([np.linspace(kmin, kmax, 1_000_001), rng.uniform(-50, 50, 500_000),
+                        rng.uniform(-745.2, -708.0, 200_000), np.array(
+                            [0.0, -0.0, 1e-300, -1e-300, kmax, np.nextafter(kmax, 1e9), kmin,
+                             np.nextafter(kmin, -1e9), -708.4, -1e10, 1e10, np.inf, -np.inf,
+                             np.nan])])
+    dx = torch.tensor(x, dtype=torch.float64, device="cuda")
+    dy, dr = torch.empty_like(dx), torch.empty_like(dx)
+    assert m.fp64_exp_eval(dx.data_ptr(), dy.data_ptr(), dr.data_ptr(), len(x),
+                           torch.cuda.current_stream().cuda_stream) == 0
+    torch.cuda.synchronize()
+    y, ref = dy.cpu().numpy(), dr.cpu().numpy()
+    with np.errstate(over="ignore"):
+        npref = np.exp(x)
+    special = ~np.isfinite(npref) | (npref == 0) | np.isnan(x)
+    assert np.array_equal(np.isnan(y), np.isnan(npref))
+    assert np.array_equal(y[special & ~np.isnan(x)], npref[special & ~np.isnan(x)])
+    ok = ~special
+    for r in (ref[ok], npref[ok]):
+        # distance in units in the last place (subnormals: units of 2^-1074)
+        ulp = np.maximum(np.spacing(np.abs(r)), np.finfo(float).smallest_subnormal)
+        assert np.max(np.abs(y[ok] - r) / ulp) <= 2.0
+    assert y[np.where(x == 0.0)[0][0]] == 1.0
+
+
 # ---------------------------------------------------------------- FP64 parity
 def test_fp64_lepage_gauss_d4_run():
     """The d=4 Lepage Gaussian, 5 adapting iterations of 1e5 (a=0.1, 50 bins)."""
