@@ -478,6 +478,22 @@ def test_fp32_gauss_d8_close_to_fp64_gpu():
 
 
 @pytest.mark.parametrize("mode", [V.VEGAS_FP64, V.VEGAS_FP32_EVAL])
+@pytest.mark.parametrize("fid", [W.GENZ_DISC, W.GENZ_PPEAK])
+def test_genz_16d_runs_reach_one(mode, fid):
+    """Table 1's 16-dimensional Genz rows (Eq. 2 and Eq. 3, normalised to
+    integrate to 1), with seeded parameters: 10 adapting iterations of 1e6 and
+    5 fixed-grid iterations of 1e7 combine to 1 within 5 sigma, sigma < 1e-3."""
+    p = W.genz_params(16, seed=16, kind=fid)
+    v = V.Vegas(16, 50, 16, mode, fid, p, max_iters=16)
+    v.run([(1_000_000, 1)] * 10 + [(10_000_000, 0)] * 5)
+    mean, sigma, chi2, k, bad = v.result(10)
+    v.close()
+    assert k == 15 and not bad
+    assert sigma < 1e-3, sigma
+    assert abs(mean - 1.0) < 5 * sigma, (mean, sigma)
+
+
+@pytest.mark.parametrize("mode", [V.VEGAS_FP64, V.VEGAS_FP32_EVAL])
 def test_pulls_over_seeds_are_standard_normal(mode):
     """On a frozen adapted grid, (I - I_exact)/sigma over 200 seeds has mean ~0
     and standard deviation ~1 (3-sigma bands of the sample moments)."""
