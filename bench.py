@@ -64,9 +64,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="fp64,e2e,adjoint,batch,mix16,gauss20",
+    ap.add_argument("--legs", default="fp64,e2e,adjoint,batch,mix16,gauss20,genz16",
                     help="measurements besides the headline FP32 steps (comma list of "
-                         "fp64, e2e, adjoint, batch, mix16, gauss20; '' for none)")
+                         "fp64, e2e, adjoint, batch, mix16, gauss20, genz16; '' for none)")
     return ap.parse_args()
 
 
@@ -400,6 +400,34 @@ def gauss20_timing(V, stream):
     return res
 
 
+def genz16_timing(V, stream):
+    """Table 1's 16-dimensional Genz integrands (Eq. 2 discontinuous, Eq. 3
+    product peak, normalised to 1; seeded a_i, c_i), 50 bins, on the d=8
+    workload's schedule (10 x 1e7 adapting, 5 x 1e8 fixed) in both precisions;
+    the result combines the fixed-grid iterations and is compared with 1."""
+    import torch
+
+    from paper_2002_12921_b300 import workloads as W
+
+    res = {}
+    for fname, fid in (("genz_disc", V.VEGAS_GENZ_DISC), ("genz_ppeak", V.VEGAS_GENZ_PPEAK)):
+        p = W.genz_params(16, seed=16, kind=fid)
+        res[fname] = {}
+        for name, mode in (("fp32", V.VEGAS_FP32_EVAL), ("fp64", V.VEGAS_FP64)):
+            v = V.Vegas(16, NBINS, 16, mode, fid, p, max_iters=IT_ADAPT + IT_FIXED, stream=stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            v.run([(N_ADAPT, 1)] * IT_ADAPT + [(N_FIXED, 0)] * IT_FIXED, ALPHA)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            m, sg, c2, n, bad = v.result(IT_ADAPT)
+            v.close()
+            res[fname][name] = {"ms": ms, "samples_per_s": SAMPLES_PER_STEP / (ms / 1e3),
+                                "mean": m, "sigma": sg, "chi2_dof": c2, "pull": (m - 1.0) / sg}
+    return res
+
+
 def e2e_mode(V, mode, steps, seed0, ws, stream):
     """Same workload through the public API with host buffers: per step the
     starting grid and the integrand parameters come from pinned host memory and
@@ -586,6 +614,7 @@ def main():
     batch = batch_timing(V, stream) if rank == 0 and "batch" in legs else None
     mix16 = mix16_timing(V, stream) if rank == 0 and "mix16" in legs else None
     gauss20 = gauss20_timing(V, stream) if rank == 0 and "gauss20" in legs else None
+    genz16 = genz16_timing(V, stream) if rank == 0 and "genz16" in legs else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -626,6 +655,7 @@ def main():
             "batch_256_gauss_8iters": batch,
             "mix2_d16_N100_1e9_per_iter": mix16,
             "symgauss_d20_a0.1_N50_10x1e7adapt+5x1e8fixed": gauss20,
+            "genz_d16_N50_10x1e7adapt+5x1e8fixed": genz16,
             "result": result,
         }
         print(json.dumps(line), flush=True)
