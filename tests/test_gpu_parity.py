@@ -493,6 +493,28 @@ def test_genz_16d_runs_reach_one(mode, fid):
     assert abs(mean - 1.0) < 5 * sigma, (mean, sigma)
 
 
+@pytest.mark.parametrize("fid", [W.GENZ_DISC, W.GENZ_PPEAK])
+def test_genz_pulls_over_seeds_are_standard_normal(fid):
+    """16-d Genz on a frozen adapted grid (FP32): (I - 1)/sigma over 200 seeds
+    has mean ~0 and standard deviation ~1 (3-sigma bands)."""
+    p = W.genz_params(16, seed=16, kind=fid)
+    warm = V.Vegas(16, 50, 16, V.VEGAS_FP64, fid, p, max_iters=8)
+    warm.run([(1_000_000, 1)] * 6)
+    grid = warm.grid()
+    warm.close()
+    pulls = []
+    for seed in range(200):
+        v = V.Vegas(16, 50, 5000 + seed, V.VEGAS_FP32_EVAL, fid, p, max_iters=2)
+        v.set_grid(grid)
+        v.iterate(200_000, 0)
+        row = v.iterations()[0]
+        v.close()
+        pulls.append((row[4] - 1.0) / np.sqrt(row[5]))
+    pulls = np.array(pulls)
+    assert abs(pulls.mean()) < 3 / np.sqrt(200)
+    assert abs(pulls.std() - 1) < 3 / np.sqrt(2 * 200)
+
+
 @pytest.mark.parametrize("mode", [V.VEGAS_FP64, V.VEGAS_FP32_EVAL])
 def test_pulls_over_seeds_are_standard_normal(mode):
     """On a frozen adapted grid, (I - I_exact)/sigma over 200 seeds has mean ~0
