@@ -270,7 +270,7 @@ class Vegas:
                  stream=None):
         import torch
 
-        self.dim, self.nbins = dim, nbins
+        self.dim, self.nbins, self.max_iters = dim, nbins, max_iters
         self.ws_bytes = vegas_workspace_bytes(dim, nbins, max_iters)
         self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.workspace.device)
@@ -303,7 +303,7 @@ class Vegas:
         dim, nbins = struct.unpack_from("<QQ", blob, 16)
         (max_iters,) = struct.unpack_from("<Q", blob, 48)
         self = cls.__new__(cls)
-        self.dim, self.nbins = int(dim), int(nbins)
+        self.dim, self.nbins, self.max_iters = int(dim), int(nbins), int(max_iters)
         self.ws_bytes = vegas_workspace_bytes(self.dim, self.nbins, int(max_iters))
         self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(
@@ -322,11 +322,11 @@ class Vegas:
         return vegas_result(self.handle, first_iter)
 
     def iterations(self):
-        return vegas_get_iterations(self.handle)
+        return vegas_get_iterations(self.handle, self.max_iters)
 
     def iteration_times(self):
         """Device time of each logged iteration, ns."""
-        return vegas_get_iteration_times(self.handle)
+        return vegas_get_iteration_times(self.handle, self.max_iters)
 
     def grid(self):
         return vegas_get_grid(self.handle, self.dim, self.nbins)
