@@ -542,12 +542,14 @@ def main():
 
     import paper_2002_12921_b300 as V
 
-    torch.cuda.set_device(local)
+    # one rank per GPU; ranks beyond the visible devices share them (only with a
+    # host-side backend, for exercising this path on fewer GPUs)
+    torch.cuda.set_device(local % torch.cuda.device_count())
     dist = None
     if world > 1:
         import torch.distributed as dist
 
-        dist.init_process_group("nccl")
+        dist.init_process_group(os.environ.get("VEGAS_BENCH_DIST_BACKEND", "nccl"))
     V.lib()
     stream = torch.cuda.current_stream()
     ws = torch.empty(V.vegas_workspace_bytes(DIM, NBINS, IT_ADAPT + IT_FIXED), dtype=torch.uint8,
