@@ -95,7 +95,8 @@ def test_philox_words_bit_exact():
     of the sample index, for several dims, iterations and integral ids."""
     for seed, ident, it, i0, n, dim in [(1, 0, 0, 0, 4096, 8), (0xDEADBEEF12345678, 3, 7,
                                         2**32 - 1000, 2000, 5), (2**64 - 1, 255, 2**32 - 1, 2**40,
-                                        700, 16), (42, 1, 1, 12345, 1001, 1)]:
+                                        700, 16), (42, 1, 1, 12345, 1001, 1),
+                                       (7, 9, 3, 2**32 - 500, 1000, 20)]:
         out = torch.empty((n, dim), dtype=torch.int32, device="cuda")
         V.vegas_sample_words(seed, ident, it, i0, n, dim, out.data_ptr(),
                              torch.cuda.current_stream().cuda_stream)
