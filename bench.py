@@ -325,7 +325,8 @@ def batch_timing(V, stream, reps=5):
         B.close()
         res[name] = {"graph_ms": times["graph"], "eager_ms": times["eager"],
                      "samples_per_s": total / (times["graph"] / 1e3),
-                     "block_threads": choice[0], "tile_samples": choice[1]}
+                     "block_threads": choice[0], "tile_samples": choice[1],
+                     "tiles_by_dim": {str(d): t for d, t in sorted(choice[2].items())}}
     return res
 
 

@@ -266,6 +266,13 @@ int vegas_batch_init(vegas_batch **out, int count, const int *dims, const uint64
 /* Block size (32..256, multiple of 32) and samples per tile (>= 4096, multiple
  * of 32); 0 keeps the current value.  Rebuilds the tile table. */
 int vegas_batch_set_config(vegas_batch *b, int block_threads, uint64_t tile_samples);
+/* Samples per tile by dimension: tiles[d-1] for the integrals of dimension d
+ * (d = 1 .. count, count <= VEGAS_MAX_DIM; each 0 = the vegas_batch_set_config
+ * size, else >= 4096 and a multiple of 32); tiles == NULL with count 0 clears
+ * them.  Work per sample grows with the dimension, so smaller tiles for wide
+ * integrals even out the blocks' loads.  Rebuilds the tile table; results do
+ * not depend on it. */
+int vegas_batch_set_tiles_by_dim(vegas_batch *b, const uint64_t *tiles, int count);
 /* Order the batch's work on another stream (for graph capture on a side stream). */
 int vegas_batch_set_stream(vegas_batch *b, void *cuda_stream);
 /* Uniform grids, cleared histograms and logs, iteration counter 0 (device work

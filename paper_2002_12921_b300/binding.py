@@ -31,7 +31,8 @@ EXPORTED = ("vegas_workspace_bytes", "vegas_init_grid", "vegas_set_config", "veg
             "vegas_batch_result", "vegas_batch_get_log", "vegas_batch_get_grid",
             "vegas_batch_destroy", "vegas_iterate_range", "vegas_shard_export",
             "vegas_shard_import", "vegas_export_state", "vegas_import_state",
-            "vegas_set_user_integrand", "vegas_get_iteration_times")
+            "vegas_set_user_integrand", "vegas_get_iteration_times",
+            "vegas_batch_set_tiles_by_dim")
 
 
 class VegasError(RuntimeError):
@@ -81,6 +82,7 @@ def lib():
         L.vegas_batch_init.argtypes = [ctypes.POINTER(vp), i32, vp, vp, i32, u64, i32, vp, i32,
                                        vp, sz, vp]
         L.vegas_batch_set_config.argtypes = [vp, i32, u64]
+        L.vegas_batch_set_tiles_by_dim.argtypes = [vp, vp, i32]
         L.vegas_batch_set_stream.argtypes = [vp, vp]
         L.vegas_batch_reset.argtypes = [vp]
         L.vegas_batch_iterate.argtypes = [vp, i32, dbl]
@@ -418,6 +420,15 @@ class VegasBatch:
         _check(lib().vegas_batch_set_config(self.handle, block_threads, tile_samples),
                "vegas_batch_set_config")
 
+    def config_tiles_by_dim(self, tiles):
+        """Samples per tile by dimension: {dim: samples} (0 or absent: the
+        set_config size); an empty dict clears them."""
+        arr = (ctypes.c_uint64 * VEGAS_MAX_DIM)()
+        for d, t in tiles.items():
+            arr[int(d) - 1] = int(t)
+        _check(lib().vegas_batch_set_tiles_by_dim(self.handle, arr, VEGAS_MAX_DIM),
+               "vegas_batch_set_tiles_by_dim")
+
     def set_stream(self, stream):
         self.stream = stream
         _check(lib().vegas_batch_set_stream(self.handle, stream.cuda_stream),
@@ -520,28 +531,51 @@ def autotune(dim, nbins, mode, integrand, params, n, adapt=False, blocks=(128, 2
 
 
 def autotune_batch(batch, blocks=(128, 256), tiles=(8192, 16384, 32768, 65536, 131072), reps=2,
-                   alpha=1.5):
-    """Pick (block_threads, tile_samples) for a batch by timing one adapting
+                   alpha=1.5, buckets=((1, 4), (5, 8), (9, 12), (13, 16), (17, 20))):
+    """Pick the launch configuration of a batch by timing one adapting
     iteration of every integral per candidate (CUDA events on the batch's
-    stream, best of `reps`).  Leaves the batch configured with the winner and
-    reset; returns (best, {candidate: ms})."""
+    stream, best of `reps`): first (block_threads, tile_samples) for the whole
+    batch, then, one dimension bucket at a time, a tile size for the integrals
+    of that bucket (half or twice the batch's, kept if faster).  Leaves the
+    batch configured with the winner and reset; returns
+    ((block_threads, tile_samples, {dim: tile}), {candidate: ms})."""
     import torch
 
+    def time_one():
+        best = float("inf")
+        for _ in range(reps):
+            batch.reset()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(batch.stream)
+            batch.iterate(True, alpha)
+            e1.record(batch.stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
     timings = {}
+    batch.config_tiles_by_dim({})
     for bt in blocks:
         for ts in tiles:
             batch.config(block_threads=bt, tile_samples=ts)
-            best = float("inf")
-            for _ in range(reps):
-                batch.reset()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(batch.stream)
-                batch.iterate(True, alpha)
-                e1.record(batch.stream)
-                e1.synchronize()
-                best = min(best, e0.elapsed_time(e1))
-            timings[(bt, ts)] = best
-    choice = min(timings, key=timings.get)
-    batch.config(block_threads=choice[0], tile_samples=choice[1])
+            timings[(bt, ts)] = time_one()
+    bt, ts = min(timings, key=timings.get)
+    batch.config(block_threads=bt, tile_samples=ts)
+    best_ms, by_dim = timings[(bt, ts)], {}
+    present = set(batch.dims)
+    for lo, hi in buckets:
+        dims = [d for d in range(lo, hi + 1) if d in present]
+        if not dims:
+            continue
+        for cand in (ts // 2, ts * 2):
+            if cand < 4096:
+                continue
+            trial = {**by_dim, **{d: cand for d in dims}}
+            batch.config_tiles_by_dim(trial)
+            ms = time_one()
+            timings[(bt, ts, (lo, hi), cand)] = ms
+            if ms < best_ms:
+                best_ms, by_dim = ms, trial
+        batch.config_tiles_by_dim(by_dim)
     batch.reset()
-    return choice, timings
+    return (bt, ts, by_dim), timings

@@ -167,6 +167,7 @@ struct vegas_batch {
     int max_dim;
     int block_threads;
     uint64_t tile_samples;
+    uint64_t tile_by_dim[kMaxDim + 1];  // per dimension; 0: tile_samples
     unsigned num_tiles;
     int iters;  // iterations enqueued since the last reset
     uint32_t rk0[10], rk1[10];
@@ -205,14 +206,17 @@ T* at(const vegas_batch* b, size_t off) {
 // other blocks wait, are then the short ones.
 int build_tiles(vegas_batch* b) {
     b->tiles.clear();
-    for (int i = 0; i < b->count; ++i)
-        for (uint64_t s = 0; s < b->n[i]; s += b->tile_samples) {
+    for (int i = 0; i < b->count; ++i) {
+        const uint64_t ts = b->tile_by_dim[b->dims[i]] ? b->tile_by_dim[b->dims[i]]
+                                                       : b->tile_samples;
+        for (uint64_t s = 0; s < b->n[i]; s += ts) {
             BatchTile t;
             t.b = (unsigned)i;
             t.start = s;
-            t.count = (unsigned)((b->n[i] - s) < b->tile_samples ? (b->n[i] - s) : b->tile_samples);
+            t.count = (unsigned)((b->n[i] - s) < ts ? (b->n[i] - s) : ts);
             b->tiles.push_back(t);
         }
+    }
     std::stable_sort(b->tiles.begin(), b->tiles.end(), [b](const BatchTile& x, const BatchTile& y) {
         return (uint64_t)x.count * b->dims[x.b] > (uint64_t)y.count * b->dims[y.b];
     });
@@ -285,6 +289,7 @@ int vegas_batch_init(vegas_batch** out, int count, const int* dims, const uint64
     b->L = L;
     b->block_threads = 256;
     b->tile_samples = kDefaultTile;
+    for (int d = 0; d <= kMaxDim; ++d) b->tile_by_dim[d] = 0;
     b->iters = 0;
     philox_round_keys(seed, b->rk0, b->rk1);
     b->dims.assign(dims, dims + count);
@@ -354,6 +359,19 @@ int vegas_batch_set_config(vegas_batch* b, int block_threads, uint64_t tile_samp
         if (cudaStreamSynchronize(b->stream) != cudaSuccess) return VEGAS_ECUDA;
     }
     return VEGAS_OK;
+}
+
+int vegas_batch_set_tiles_by_dim(vegas_batch* b, const uint64_t* tiles, int count) {
+    if (!b || count < 0 || count > kMaxDim || (count > 0 && !tiles)) return VEGAS_EINVAL;
+    for (int d = 0; d < count; ++d)
+        if (tiles[d] && (tiles[d] < kMinTile || tiles[d] % 32 || tiles[d] > (1ull << 31)))
+            return VEGAS_EINVAL;
+    for (int d = 1; d <= kMaxDim; ++d) b->tile_by_dim[d] = d <= count ? tiles[d - 1] : 0;
+    Dev g(b->device);
+    if (!g.ok) return VEGAS_ECUDA;
+    const int rc = build_tiles(b);
+    if (rc != VEGAS_OK) return rc;
+    return cudaStreamSynchronize(b->stream) == cudaSuccess ? VEGAS_OK : VEGAS_ECUDA;
 }
 
 int vegas_batch_set_stream(vegas_batch* b, void* cuda_stream) {

@@ -120,15 +120,37 @@ def test_graph_replay_equals_eager_run(mode):
 def test_autotuner_picks_a_candidate_and_keeps_results():
     dims, ns, params = small_batch()
     B = V.VegasBatch(dims, ns, 30, 17, V.VEGAS_FP64, params, max_iters=4)
-    choice, timings = V.binding.autotune_batch(B, blocks=(128, 256), tiles=(4096, 16384),
-                                               reps=1)
-    assert choice in timings and len(timings) == 4
+    (bt, ts, by_dim), timings = V.binding.autotune_batch(B, blocks=(128, 256),
+                                                         tiles=(4096, 16384), reps=1)
+    assert (bt, ts) in timings and len(timings) >= 4
+    assert all(d in dims and t >= 4096 for d, t in by_dim.items())
     B.run(2)
     tuned = B.log()[:, :2, 4]
     B.config(block_threads=256, tile_samples=4096)
+    B.config_tiles_by_dim({})
     B.run(2)
     assert np.allclose(B.log()[:, :2, 4], tuned, rtol=1e-12)
     B.close()
+
+
+def test_tiles_by_dimension_do_not_change_results():
+    dims, ns, params = small_batch()
+    logs = []
+    for by_dim in ({}, {2: 4096, 8: 65536, 16: 8192, 20: 4096}):
+        B = V.VegasBatch(dims, ns, 30, 19, V.VEGAS_FP64, params, max_iters=4)
+        B.config_tiles_by_dim(by_dim)
+        B.run(3)
+        logs.append((B.log()[:, :3, 4], np.concatenate([B.grid(b).ravel()
+                                                        for b in range(len(dims))])))
+        B.close()
+    assert np.allclose(logs[1][0], logs[0][0], rtol=1e-12, atol=0)
+    assert np.allclose(logs[1][1], logs[0][1], rtol=1e-12, atol=1e-15)
+    with pytest.raises(V.VegasError):
+        B = V.VegasBatch(dims, ns, 30, 19, V.VEGAS_FP64, params, max_iters=4)
+        try:
+            B.config_tiles_by_dim({3: 1000})  # below the 4096 minimum
+        finally:
+            B.close()
 
 
 def _combine(I, var):
