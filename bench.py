@@ -493,6 +493,13 @@ def cpu_baseline(fast=False):
         n1 = sum(s for s, _ in sched1)
         out["single_core"] = {"value": n1 / dt1, "unit": "samples/s",
                               "sample": f"{n1:.1e} samples (1e6 adapting + 2e6 fixed), 1 thread"}
+        # the d=16 two-peak mixture: one adapting iteration of 2e6 samples
+        wl = W.c5_mix16()
+        t0 = time.perf_counter()
+        oracle.run(16, 100, wl.seed, W.GAUSS_MIX2, wl.params, [(2_000_000, 1)], nthreads=cores)
+        out["mix16"] = {"value": 2_000_000 / (time.perf_counter() - t0), "unit": "samples/s",
+                        "sample": "d=16 mixture, one adapting iteration of 2e6 samples, "
+                                  f"{cores} threads"}
     return out
 
 
@@ -632,7 +639,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline()
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu_model",
-                                  "single_core")}
+                                  "single_core", "mix16")}
 
     if rank == 0:
         m32, s32 = res32[0], res32[1]
