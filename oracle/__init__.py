@@ -41,6 +41,9 @@ def lib():
         L.oracle_iterate_range.argtypes = [i32, i32, vp, u64, u32, u32, u64, u64, i32, vp, i32,
                                            i32, vp, vp, vp, vp]
         L.oracle_iterate_range.restype = i32
+        L.oracle_iterate_range_box.argtypes = [i32, i32, vp, u64, u32, u32, u64, u64, i32, vp,
+                                               vp, vp, i32, i32, vp, vp, vp, vp]
+        L.oracle_iterate_range_box.restype = i32
         L.oracle_estimate.argtypes = [dbl, dbl, u64, vp, vp]
         L.oracle_estimate.restype = None
         L.oracle_damp.argtypes = [dbl, dbl]
@@ -112,8 +115,17 @@ def integrand(fid, params, x):
     return f
 
 
-def iterate(edges, seed, it, n, fid, params, adapt, integral_id=0, nthreads=1):
-    """One iteration: returns dict(S1, S2, nonfinite, hist (d x N) or None, I, var)."""
+def _box(box, dim):
+    """(lo, w) arrays for a box [(lo_k, hi_k)] or (None, None) for the unit cube."""
+    if box is None:
+        return None, None
+    b = np.asarray(box, dtype=np.float64).reshape(dim, 2)
+    return _c(b[:, 0], np.float64), _c(b[:, 1] - b[:, 0], np.float64)
+
+
+def iterate(edges, seed, it, n, fid, params, adapt, integral_id=0, nthreads=1, box=None):
+    """One iteration: returns dict(S1, S2, nonfinite, hist (d x N) or None, I, var).
+    box: [(lo_k, hi_k)] per dimension (None: the unit cube)."""
     edges = _c(edges, np.float64)
     dim, nb1 = edges.shape
     nbins = nb1 - 1
@@ -122,9 +134,10 @@ def iterate(edges, seed, it, n, fid, params, adapt, integral_id=0, nthreads=1):
     S1 = np.zeros(1)
     S2 = np.zeros(1)
     bad = np.zeros(1, dtype=np.uint64)
-    rc = lib().oracle_iterate(dim, nbins, _ptr(edges), seed, integral_id, it, n, fid, _ptr(p),
-                              1 if adapt else 0, nthreads, _ptr(S1), _ptr(S2), _ptr(hist),
-                              _ptr(bad))
+    lo, w = _box(box, dim)
+    rc = lib().oracle_iterate_range_box(dim, nbins, _ptr(edges), seed, integral_id, it, 0, n,
+                                        fid, _ptr(p), _ptr(lo), _ptr(w), 1 if adapt else 0,
+                                        nthreads, _ptr(S1), _ptr(S2), _ptr(hist), _ptr(bad))
     if rc != 0:
         raise ValueError("oracle_iterate: invalid arguments")
     I, var = estimate(S1[0], S2[0], n)
@@ -200,7 +213,7 @@ def gauss_gradient(edges, seed, it, n, params):
 
 
 def run(dim, nbins, seed, fid, params, schedule, alpha=1.5, integral_id=0, nthreads=1,
-        edges=None, first_iter=0):
+        edges=None, first_iter=0, box=None):
     """A whole Vegas run.  schedule: list of (n_samples, adapt) per iteration.
     Each adapting iteration is followed by a refinement of the grid.
     Returns dict(log=[iteration dicts], edges=final grid, grids=[grid used per
@@ -209,7 +222,7 @@ def run(dim, nbins, seed, fid, params, schedule, alpha=1.5, integral_id=0, nthre
     log, grids = [], []
     for it, (n, adapt) in enumerate(schedule):
         grids.append(e.copy())
-        r = iterate(e, seed, it, n, fid, params, adapt, integral_id, nthreads)
+        r = iterate(e, seed, it, n, fid, params, adapt, integral_id, nthreads, box)
         r["n"] = n
         log.append(r)
         if adapt:

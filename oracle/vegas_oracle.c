@@ -227,6 +227,7 @@ double oracle_integrand(int id, int dim, const double *params, const double *x)
 typedef struct {
     int dim, nbins, integrand, adapt;
     const double *edges, *params;
+    const double *box_lo, *box_w; /* integration box (NULL: the unit cube) */
     uint64_t seed, begin, end;
     uint32_t integral_id, iter;
     long double s1, s2;
@@ -244,6 +245,11 @@ static void *run_slice(void *arg)
         double J;
         oracle_sample_words(jb->seed, jb->integral_id, jb->iter, i, jb->dim, words);
         oracle_map_sample(jb->dim, jb->nbins, jb->edges, words, x, &J, bins);
+        if (jb->box_lo) /* the box [lo, lo + w]: x = lo + w u, dx = (prod w) du */
+            for (int k = 0; k < jb->dim; ++k) {
+                x[k] = jb->box_lo[k] + jb->box_w[k] * x[k];
+                J *= jb->box_w[k];
+            }
         double fw = oracle_integrand(jb->integrand, jb->dim, jb->params, x) * J;
         if (!isfinite(fw)) {
             jb->nonfinite++;
@@ -260,16 +266,20 @@ static void *run_slice(void *arg)
 }
 
 /* One Vegas iteration over sample indices [first, first + n) (the whole
- * iteration when first = 0 and n is its sample count; a shard otherwise).  Outputs the sums S1, S2, the
+ * iteration when first = 0 and n is its sample count; a shard otherwise), over
+ * the box [lo, lo + w] (box_lo, box_w: dim doubles each; NULL: the unit cube --
+ * the grid stays in unit coordinates u and the integrand sees x = lo + w u with
+ * the Jacobian's extra factor prod w).  Outputs the sums S1, S2, the
  * count of non-finite f*J values (left out of the sums), and, when adapt != 0,
  * adds the histogram sum over samples of (fJ)^2 per (dimension, bin) into hist
  * (dim * nbins doubles, caller-initialised).  The index range is cut into
  * nthreads contiguous slices whose sums are added in slice order.
  * Returns 0, or -1 on invalid arguments. */
-int oracle_iterate_range(int dim, int nbins, const double *edges, uint64_t seed,
-                         uint32_t integral_id, uint32_t iter, uint64_t first, uint64_t n,
-                         int integrand, const double *params, int adapt, int nthreads,
-                         double *S1, double *S2, double *hist, uint64_t *nonfinite)
+int oracle_iterate_range_box(int dim, int nbins, const double *edges, uint64_t seed,
+                             uint32_t integral_id, uint32_t iter, uint64_t first, uint64_t n,
+                             int integrand, const double *params, const double *box_lo,
+                             const double *box_w, int adapt, int nthreads, double *S1,
+                             double *S2, double *hist, uint64_t *nonfinite)
 {
     if (dim < 1 || dim > ORACLE_MAX_DIM || nbins < 1 || nthreads < 1) return -1;
     if (nthreads > 256) nthreads = 256;
@@ -282,6 +292,7 @@ int oracle_iterate_range(int dim, int nbins, const double *edges, uint64_t seed,
         slice_job *jb = &jobs[t];
         jb->dim = dim; jb->nbins = nbins; jb->integrand = integrand; jb->adapt = adapt;
         jb->edges = edges; jb->params = params; jb->seed = seed;
+        jb->box_lo = box_lo; jb->box_w = box_w;
         jb->integral_id = integral_id; jb->iter = iter;
         /* slice t is [floor(n t / T), floor(n (t+1) / T)) */
         jb->begin = first + (uint64_t)(((unsigned __int128)n * (uint64_t)t) / (uint64_t)nthreads);
@@ -315,6 +326,16 @@ int oracle_iterate_range(int dim, int nbins, const double *edges, uint64_t seed,
     free(jobs);
     free(tids);
     return 0;
+}
+
+int oracle_iterate_range(int dim, int nbins, const double *edges, uint64_t seed,
+                         uint32_t integral_id, uint32_t iter, uint64_t first, uint64_t n,
+                         int integrand, const double *params, int adapt, int nthreads,
+                         double *S1, double *S2, double *hist, uint64_t *nonfinite)
+{
+    return oracle_iterate_range_box(dim, nbins, edges, seed, integral_id, iter, first, n,
+                                    integrand, params, NULL, NULL, adapt, nthreads, S1, S2, hist,
+                                    nonfinite);
 }
 
 int oracle_iterate(int dim, int nbins, const double *edges, uint64_t seed, uint32_t integral_id,

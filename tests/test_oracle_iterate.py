@@ -226,3 +226,47 @@ def test_small_n_estimate_is_textbook_mean_and_variance(n):
     r = oracle.iterate(e, seed, it, n, W.GAUSS, p, adapt=False)
     assert abs(r["I"] - fw.mean()) <= 1e-14 * abs(fw.mean())
     assert abs(r["var"] - np.var(fw, ddof=1) / n) <= 1e-12 * np.var(fw, ddof=1) / n
+
+
+# ---------------------------------------------------------------- box domains
+def test_box_flat_gives_the_volume_exactly():
+    """f = 1 over a box on the uniform grid: every f J is the volume (up to the
+    rounding of the bin widths), so I is the volume and var vanishes."""
+    box = [(-1.0, 2.0), (0.25, 0.5), (3.0, 10.0)]
+    vol = 3.0 * 0.25 * 7.0
+    r = oracle.iterate(oracle.uniform_grid(3, 16), 5, 0, 20_000, W.FLAT, [], True, box=box)
+    assert abs(r["I"] - vol) <= 1e-13 * vol and r["var"] <= 1e-25
+    assert np.allclose(r["hist"].sum(axis=1), 20_000 * vol ** 2, rtol=1e-13)
+
+
+def test_unit_box_equals_no_box():
+    p = W.gauss_params(4, 0.2, [0.3, 0.4, 0.6, 0.7])
+    e = W.random_monotone_grid(4, 20, seed=4)
+    a = oracle.iterate(e, 9, 2, 30_000, W.GAUSS, p, True)
+    b = oracle.iterate(e, 9, 2, 30_000, W.GAUSS, p, True, box=[(0.0, 1.0)] * 4)
+    assert a["S1"] == b["S1"] and a["S2"] == b["S2"] and np.array_equal(a["hist"], b["hist"])
+
+
+def test_box_is_the_change_of_variables_of_the_unit_cube():
+    """A Gaussian (a, mu) over [lo, lo + w]^d is, sample for sample, the
+    unit-cube Gaussian with a/w and (mu - lo)/w: the same counters give the
+    same sums up to rounding."""
+    lo, w, a = -0.7, 2.5, 0.4
+    mu = np.array([0.1, 0.5, 1.2])
+    e = W.random_monotone_grid(3, 25, seed=7)
+    boxed = oracle.iterate(e, 3, 1, 40_000, W.GAUSS, W.gauss_params(3, a, mu), False,
+                           box=[(lo, lo + w)] * 3)
+    unit = oracle.iterate(e, 3, 1, 40_000, W.GAUSS, W.gauss_params(3, a / w, (mu - lo) / w),
+                          False)
+    assert abs(boxed["S1"] - unit["S1"]) <= 1e-12 * unit["S1"]
+    assert abs(boxed["S2"] - unit["S2"]) <= 1e-12 * unit["S2"]
+
+
+def test_vegas_over_a_box_reaches_the_erf_closed_form():
+    box = [(-1.0, 1.0), (0.0, 3.0), (-2.0, 0.5)]
+    mu, a = np.array([0.2, 1.0, -0.5]), 0.3
+    exact = float(np.prod([0.5 * (erf((hi - m) / a) - erf((lo - m) / a))
+                           for (lo, hi), m in zip(box, mu)]))
+    r = oracle.run(3, 40, 11, W.GAUSS, W.gauss_params(3, a, mu), [(100_000, 1)] * 6,
+                   nthreads=4, first_iter=2, box=box)
+    assert abs(r["mean"] - exact) < 5 * r["sigma"] and r["sigma"] < 1e-3 * exact
