@@ -138,6 +138,15 @@ int vegas_init_grid(vegas_state **out, int dim, int nbins, uint64_t seed, int mo
                     const double *params, int nparams, int max_iters, void *d_workspace,
                     size_t ws_bytes, void *cuda_stream);
 
+/* Integrate over the box [lo_k, hi_k] (dim doubles each, finite, hi > lo)
+ * instead of the unit cube: the grid stays in unit coordinates u, the integrand
+ * is evaluated at x = lo + (hi - lo) u and the Jacobian gains prod (hi - lo).
+ * The integrand's parameters keep their meaning in x (e.g. the Gaussian's
+ * centres and width); a caller-compiled integrand receives x.  Only before the
+ * first iteration (else VEGAS_ESTATE); VEGAS_EINVAL on a bad box.  States with a
+ * box are checkpointed with it; vegas_gauss_adjoint refuses them. */
+int vegas_set_box(vegas_state *s, const double *lo, const double *hi);
+
 /* Change the launch configuration (cfg == NULL restores the defaults). */
 int vegas_set_config(vegas_state *s, const vegas_config *cfg);
 
@@ -332,14 +341,16 @@ int vegas_iterate_noalloc(double *d_edges, int dim, int nbins, uint64_t seed, ui
 /* ---- checkpoint / resume -------------------------------------------------- */
 /* A state's resumable content as a flat little-endian blob: shape, mode,
  * integrand and its parameters, seed, iteration count, launch configuration,
- * the grid, the histogram (an adapting iteration not yet refined) and the
- * iteration log.  Because every sample is a function of (seed, iteration,
+ * the grid, the histogram (an adapting iteration not yet refined), the
+ * iteration log and the box (vegas_set_box; format version 2, version-1 blobs
+ * without a box are still read).  Because every sample is a function of (seed, iteration,
  * index), a state imported from a blob continues exactly as the exported one
  * would have.  Export synchronises the stream.  With buf == NULL, *bytes
  * receives the blob size; otherwise *bytes must hold at least that size. */
 int vegas_export_state(vegas_state *s, void *buf, size_t *bytes);
-/* Create a state from a blob (VEGAS_EINVAL if it is malformed -- including a
- * grid vegas_set_grid would refuse -- or of another
+/* Create a state from a blob of exactly `bytes` bytes (VEGAS_EINVAL if it is
+ * malformed -- including a size other than its header implies and a grid
+ * vegas_set_grid would refuse -- or of another
  * format version) on a caller workspace of at least vegas_workspace_bytes()
  * for the blob's shape and iteration capacity.  Asynchronous on the stream. */
 int vegas_import_state(vegas_state **out, const void *buf, size_t bytes, void *d_workspace,

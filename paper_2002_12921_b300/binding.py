@@ -32,7 +32,7 @@ EXPORTED = ("vegas_workspace_bytes", "vegas_init_grid", "vegas_set_config", "veg
             "vegas_batch_destroy", "vegas_iterate_range", "vegas_shard_export",
             "vegas_shard_import", "vegas_export_state", "vegas_import_state",
             "vegas_set_user_integrand", "vegas_get_iteration_times",
-            "vegas_batch_set_tiles_by_dim")
+            "vegas_batch_set_tiles_by_dim", "vegas_set_box")
 
 
 class VegasError(RuntimeError):
@@ -65,6 +65,7 @@ def lib():
         L.vegas_init_grid.argtypes = [ctypes.POINTER(vp), i32, i32, u64, i32, i32, vp, i32, i32,
                                       vp, sz, vp]
         L.vegas_set_config.argtypes = [vp, ctypes.POINTER(vegas_config)]
+        L.vegas_set_box.argtypes = [vp, vp, vp]
         L.vegas_iterate.argtypes = [vp, u64, i32]
         L.vegas_refine.argtypes = [vp, dbl]
         L.vegas_result.argtypes = [vp, i32, dp, dp, dp, ip]
@@ -137,6 +138,13 @@ def vegas_set_config(h, block_threads=0, blocks_per_sm=0, min_samples_per_thread
                      chunk_samples=0):
     cfg = vegas_config(block_threads, blocks_per_sm, min_samples_per_thread, chunk_samples)
     _check(lib().vegas_set_config(h, ctypes.byref(cfg)), "vegas_set_config")
+
+
+def vegas_set_box(h, box):
+    """box: [(lo_k, hi_k)] per dimension."""
+    b = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(-1, 2))
+    lo, hi = np.ascontiguousarray(b[:, 0]), np.ascontiguousarray(b[:, 1])
+    _check(lib().vegas_set_box(h, lo.ctypes.data, hi.ctypes.data), "vegas_set_box")
 
 
 def vegas_iterate(h, n_samples, adapt):
@@ -282,6 +290,11 @@ class Vegas:
 
     def config(self, **kw):
         vegas_set_config(self.handle, **kw)
+
+    def set_box(self, box):
+        """Integrate over [(lo_k, hi_k)] instead of the unit cube (before the
+        first iteration)."""
+        vegas_set_box(self.handle, box)
 
     def set_user_integrand(self, desc, data=None, module=None):
         """Attach a VEGAS_USER_INTEGRAND descriptor (an address, e.g. from

@@ -2,10 +2,13 @@
 // flat little-endian blob (include/vegas.h).
 //
 // Layout, every field 8 bytes:
-//   magic "VEGASB3" + NUL, format version (1),
+//   magic "VEGASB3" + NUL, format version (2; version 1 blobs, without the
+//   box, are read too),
 //   dim, nbins, mode, integrand, max_iters, nparams, seed, n_iter,
 //   block_threads, blocks_per_sm, min_samples_per_thread, chunk_samples,
-//   params[nparams], edges[dim (nbins+1)], hist[dim nbins], log[n_iter x 8].
+//   has_box, unused,
+//   params[nparams], edges[dim (nbins+1)], hist[dim nbins], log[n_iter x 8],
+//   and when has_box: box_lo[dim], box_hi[dim].
 #include <cstring>
 #include <vector>
 
@@ -16,7 +19,7 @@
 namespace {
 
 constexpr char kMagic[8] = {'V', 'E', 'G', 'A', 'S', 'B', '3', 0};
-constexpr uint64_t kVersion = 1;
+constexpr uint64_t kVersion = 2;
 constexpr size_t kHeaderWords = 16;
 
 bool little_endian() {
@@ -26,9 +29,10 @@ bool little_endian() {
     return b == 1;
 }
 
-size_t blob_bytes(uint64_t dim, uint64_t nbins, uint64_t nparams, uint64_t n_iter) {
+size_t blob_bytes(uint64_t dim, uint64_t nbins, uint64_t nparams, uint64_t n_iter,
+                  bool has_box) {
     return 8 * (kHeaderWords + nparams + dim * (nbins + 1) + dim * nbins +
-                n_iter * vegas::kLogStride);
+                n_iter * vegas::kLogStride + (has_box ? 2 * dim : 0));
 }
 
 }  // namespace
@@ -48,7 +52,7 @@ extern "C" int vegas_export_state(vegas_state* s, void* buf, size_t* bytes) {
         rc = VEGAS_ECUDA;
     const uint64_t n_iter = rc == VEGAS_OK ? ctrl[kIter] : 0;
     const uint64_t dim = s->dim, nbins = s->nbins, np = s->nparams;
-    const size_t need = blob_bytes(dim, nbins, np, n_iter);
+    const size_t need = blob_bytes(dim, nbins, np, n_iter, s->has_box != 0);
     if (rc == VEGAS_OK && !buf) {
         *bytes = need;
     } else if (rc == VEGAS_OK) {
@@ -71,7 +75,8 @@ extern "C" int vegas_export_state(vegas_state* s, void* buf, size_t* bytes) {
             head[11] = (uint64_t)s->cfg.blocks_per_sm;
             head[12] = (uint64_t)s->cfg.min_samples_per_thread;
             head[13] = s->cfg.chunk_samples;
-            head[14] = head[15] = 0;
+            head[14] = s->has_box ? 1 : 0;
+            head[15] = 0;
             std::memcpy(p, head, sizeof(head));
             p += sizeof(head);
             std::memcpy(p, s->params, 8 * np);
@@ -88,6 +93,11 @@ extern "C" int vegas_export_state(vegas_state* s, void* buf, size_t* bytes) {
                 cudaMemcpyAsync(p, s->log, 8 * n_iter * kLogStride, cudaMemcpyDeviceToHost,
                                 s->stream) != cudaSuccess)
                 rc = VEGAS_ECUDA;
+            p += 8 * n_iter * kLogStride;
+            if (s->has_box) {
+                std::memcpy(p, s->box_lo, 8 * dim);
+                std::memcpy(p + 8 * dim, s->box_hi, 8 * dim);
+            }
             if (rc == VEGAS_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = VEGAS_ECUDA;
             *bytes = need;
         }
@@ -104,14 +114,16 @@ extern "C" int vegas_import_state(vegas_state** out, const void* buf, size_t byt
     if (!buf || bytes < 8 * kHeaderWords || !little_endian()) return VEGAS_EINVAL;
     uint64_t head[kHeaderWords];
     std::memcpy(head, buf, sizeof(head));
-    if (std::memcmp(&head[0], kMagic, 8) != 0 || head[1] != kVersion) return VEGAS_EINVAL;
+    if (std::memcmp(&head[0], kMagic, 8) != 0 || (head[1] != 1 && head[1] != kVersion))
+        return VEGAS_EINVAL;
+    const bool has_box = head[1] >= 2 && head[14] != 0;
     const uint64_t dim = head[2], nbins = head[3], np = head[7], n_iter = head[9];
     const uint64_t max_iters = head[6];
     if (dim < 1 || dim > (uint64_t)kMaxDim || nbins < 1 || nbins > (uint64_t)kMaxBins ||
         np > 1 + 2 * (uint64_t)kMaxDim || max_iters < 1 || max_iters > (1u << 24) ||
         n_iter > max_iters)
         return VEGAS_EINVAL;
-    if (bytes < blob_bytes(dim, nbins, np, n_iter)) return VEGAS_EINVAL;
+    if (bytes != blob_bytes(dim, nbins, np, n_iter, has_box)) return VEGAS_EINVAL;
     const unsigned char* p = static_cast<const unsigned char*>(buf) + sizeof(head);
     std::vector<double> params(np ? np : 1);
     std::memcpy(params.data(), p, 8 * np);
@@ -130,6 +142,18 @@ extern "C" int vegas_import_state(vegas_state** out, const void* buf, size_t byt
                              np ? params.data() : nullptr, (int)np, (int)max_iters, d_workspace,
                              ws_bytes, cuda_stream);
     if (rc != VEGAS_OK) return rc;
+    if (has_box) {  // after the log: box_lo[dim], box_hi[dim]
+        const unsigned char* b =
+            p + 8 * (dim * (nbins + 1) + dim * nbins + n_iter * kLogStride);
+        double lo[kMaxDim], hi[kMaxDim];
+        std::memcpy(lo, b, 8 * dim);
+        std::memcpy(hi, b + 8 * dim, 8 * dim);
+        rc = vegas_set_box(s, lo, hi);
+        if (rc != VEGAS_OK) {
+            vegas_destroy(s);
+            return VEGAS_EINVAL;
+        }
+    }
     vegas_config cfg;
     cfg.block_threads = (int)head[10];
     cfg.blocks_per_sm = (int)head[11];

@@ -443,6 +443,40 @@ static int enqueue_iteration(vegas_state* s, uint64_t begin, uint64_t end, int a
     return VEGAS_OK;
 }
 
+int vegas_set_box(vegas_state* s, const double* lo, const double* hi) {
+    if (!s) return VEGAS_EINVAL;
+    if (s->host_iters != 0) return VEGAS_ESTATE;
+    double w[kMaxDim];
+    for (int k = 0; k < s->dim; ++k) {
+        if (!lo || !hi || !std::isfinite(lo[k]) || !std::isfinite(hi[k]) || !(hi[k] > lo[k]))
+            return VEGAS_EINVAL;
+        w[k] = hi[k] - lo[k];
+        if (!std::isfinite(w[k])) return VEGAS_EINVAL;
+    }
+    // the integrand's constants afresh, then the box composed into both
+    // precisions' staging: z = sc x + sh with x = lo + w u becomes
+    // z = (sc w) u + (sc lo + sh); the staged widths then carry w, so the
+    // Jacobian gains prod w with the prefactors unchanged
+    FnConsts fc;
+    const int rc = make_consts(s->integrand, s->dim, s->nbins, s->params, s->nparams, &fc);
+    if (rc != VEGAS_OK) return rc;
+    for (int k = 0; k < s->dim; ++k)
+        for (int p = 0; p < 2; ++p) {
+            fc.sh[p][k] = fc.sc[p][k] * lo[k] + fc.sh[p][k];
+            fc.sc[p][k] *= w[k];
+        }
+    fc.user = s->fc.user;
+    s->fc = fc;
+    s->has_box = 1;
+    for (int k = 0; k < s->dim; ++k) {
+        s->box_lo[k] = lo[k];
+        s->box_hi[k] = hi[k];
+    }
+    DeviceGuard g(s->device);
+    if (!g.ok) return VEGAS_ECUDA;
+    return restage(s);
+}
+
 int vegas_set_user_integrand(vegas_state* s, const vegas_user_integrand* u, const void* d_data) {
     if (!s || !u || s->integrand != VEGAS_USER || u->dim != s->dim ||
         u->args_bytes != sizeof(IterArgs) || !u->prepare || !u->launch)

@@ -154,6 +154,8 @@ struct vegas_state {
     int nparams;
     vegas_user_integrand user;  // VEGAS_USER: the caller's kernels (launch == NULL: unset)
     float2* staged32;  // VEGAS_FP32_EVAL: the grid's staged pairs in the workspace, else null
+    int has_box;       // integration box [lo, hi] (vegas_set_box); else the unit cube
+    double box_lo[VEGAS_MAX_DIM], box_hi[VEGAS_MAX_DIM];
 };
 
 // Rewrite a float-path state's staged pairs after its edges changed other than

@@ -59,3 +59,31 @@ def test_import_refuses_a_blob_whose_grid_is_not_increasing():
     with pytest.raises(V.VegasError) as exc:
         V.Vegas.from_state(bytes(blob))
     assert exc.value.status == V.VEGAS_EINVAL
+
+
+def test_version_one_blobs_import_and_a_box_needs_version_two():
+    """Version 1 had no box: a unit-cube blob relabelled version 1 (word 14 was
+    unused and zero) resumes as before; a boxed blob relabelled version 1 has
+    2 dim words too many and is refused."""
+    import struct
+
+    p = W.gauss_params(3, 0.2)
+    for box in (None, [(-1.0, 1.0)] * 3):
+        a = V.Vegas(3, 10, 5, V.VEGAS_FP64, W.GAUSS, p, max_iters=4)
+        if box:
+            a.set_box(box)
+        a.run([(50_000, 1)])
+        blob = bytearray(a.export_state())
+        assert struct.unpack_from("<Q", blob, 8)[0] == 2
+        assert struct.unpack_from("<Q", blob, 14 * 8)[0] == (1 if box else 0)
+        struct.pack_into("<Q", blob, 8, 1)
+        if box is None:
+            struct.pack_into("<Q", blob, 14 * 8, 0)
+            b = V.Vegas.from_state(bytes(blob))
+            assert np.array_equal(b.grid(), a.grid())
+            b.close()
+        else:
+            with pytest.raises(V.VegasError) as exc:
+                V.Vegas.from_state(bytes(blob))
+            assert exc.value.status == V.VEGAS_EINVAL
+        a.close()
