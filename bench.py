@@ -46,6 +46,44 @@ ALU_PEAK_TOPS = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
 ITERATE_TRAFFIC_BYTES = 64768
 
 
+def products_per_sample(d):
+    """32x32 -> 64-bit products of one sample: Philox rounds 0 and 1 shared by
+    the sample's calls (2), rounds 2-9 of each call (16 per call), and the bin
+    split of each dimension (1)."""
+    return 2 + 16 * ((d + 3) // 4) + d
+
+
+def pipe_fractions(V, fixed_ms, adapt_ms):
+    """The measured peak of each pipe (vegas_pipe_peak, best of 3) and the
+    share of it that the d=8 FP32 iterate kernels reach: the products (the
+    binding pipe), the exponential's special-function step (one per sample)
+    and, when adapting, the histogram's float shared-memory atomic adds (d per
+    sample)."""
+    peaks = V.binding.pipe_peaks(reps=3)
+
+    def frac(name, per_sample, samples_per_s):
+        got = per_sample * samples_per_s
+        return {"per_sample": per_sample, "achieved_per_s": got, "peak_per_s": peaks[name]["per_s"],
+                "frac": got / peaks[name]["per_s"]}
+
+    fixed_rate = N_FIXED / (fixed_ms / 1e3)
+    out = {"measured": {k: {"per_s": v["per_s"], "per_sm_per_clk": v["per_sm_per_clk"],
+                            "sm_mhz": v["sm_mhz"]} for k, v in peaks.items()},
+           "basis": "vegas_pipe_peak: 8 independent chains per thread, every SM filled, "
+                    "CUDA-event time of one launch, best of 3",
+           "fixed_kernel": {"kernel": "vegas_iterate_kernel<float,8,GAUSS,fixed>",
+                            "samples_per_s": fixed_rate,
+                            "product": frac("product", products_per_sample(DIM), fixed_rate),
+                            "ex2": frac("ex2", 1, fixed_rate)}}
+    if adapt_ms:
+        adapt_rate = N_ADAPT / (adapt_ms / 1e3)
+        out["adapt_kernel"] = {"kernel": "vegas_iterate_kernel<float,8,GAUSS,adapt>",
+                               "ms_per_iteration": adapt_ms, "samples_per_s": adapt_rate,
+                               "product": frac("product", products_per_sample(DIM), adapt_rate),
+                               "atoms_f32": frac("atoms_f32", DIM, adapt_rate)}
+    return out
+
+
 def alg_ops_per_sample(d):
     """Algorithmic lane-operations of one FP32 fixed-grid sample: Philox (10
     rounds x 2 wide multiplies + 2 three-input xors per call), per dimension
@@ -239,6 +277,10 @@ def time_mode(V, mode, steps, warmup, seed0, ws, flush, stream, world=1):
     ms = [a.elapsed_time(b) for a, b in step_events]
     fixed_ms = [a.elapsed_time(b) for a, b in fixed]
     last = handles[-1]
+    # device time of each adapting iteration of the last step (the kernels'
+    # own global-timer stamps; single-GPU runs)
+    time_mode.adapt_ns = (list(V.vegas_get_iteration_times(last, IT_ADAPT + IT_FIXED)[:IT_ADAPT])
+                          if world == 1 else None)
     if world > 1:
         res = last.result(IT_ADAPT)
         for v in handles:
@@ -576,6 +618,7 @@ def main():
     ms32, fixed32, res32 = time_mode(V, V.VEGAS_FP32_EVAL, args.steps, max(3, args.warmup),
                                      seed_main, ws, flush, stream, world)
     clk = clocks.stop((time_mode.window_start, time_mode.window_end))
+    adapt32_ns = time_mode.adapt_ns
     total_ms = sum(ms32)
     if dist:
         t = torch.tensor([total_ms], device="cuda")
@@ -625,6 +668,10 @@ def main():
                 "binding_pipe": {"pipe": "fmaheavy: integer multiplies (34 Philox + 8 bin "
                                          "32x32->64 products per d=8 sample)",
                                  "busy_ncu": 0.735}}
+    if rank == 0:
+        roofline["pipes"] = pipe_fractions(V, fixed_ms, statistics.median(adapt32_ns) / 1e6
+                                           if adapt32_ns else None)
+        roofline["frac_binding_pipe_measured"] = roofline["pipes"]["fixed_kernel"]["product"]["frac"]
     if clk.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved / (SMS * LANES_PER_SM * clk["sm_mhz"] * 1e6
                                                          / 1e12)

@@ -392,6 +392,30 @@ typedef struct {
 int vegas_set_user_integrand(vegas_state *s, const vegas_user_integrand *u, const void *d_data);
 
 
+/* ---- measurement: pipe peaks ---------------------------------------------- */
+/* The peak rate of one operation the iterate kernels depend on, measured on
+ * the current device: every SM filled with blocks whose threads each run 8
+ * independent chains of the operation for `iters` steps (0: a default of about
+ * a millisecond per launch), one warm-up launch, then one launch timed with
+ * CUDA events on the stream.  out[0] = lane-operations per second, out[1] = the
+ * SM clock during the timed launch in MHz (cycle counter over global timer,
+ * read by one block), out[2] = SM count, out[3] = blocks launched.  d_scratch:
+ * caller device memory of at least VEGAS_PIPE_SCRATCH_BYTES, 8-byte aligned.
+ * Synchronises the stream.  VEGAS_EINVAL for an unknown op or a bad argument,
+ * VEGAS_ECUDA if a launch fails. */
+#define VEGAS_PIPE_FFMA 0      /* float fused multiply-add */
+#define VEGAS_PIPE_DFMA 1      /* double fused multiply-add */
+#define VEGAS_PIPE_EX2 2       /* ex2.approx.ftz.f32 */
+#define VEGAS_PIPE_PRODUCT 3   /* 32x32 -> 64-bit product as umulhi + low multiply */
+#define VEGAS_PIPE_IMAD 4      /* 32-bit multiply-add, low word */
+#define VEGAS_PIPE_LDS 5       /* 32-bit shared-memory load, conflict free */
+#define VEGAS_PIPE_ATOMS_U32 6 /* 32-bit integer atomic add to shared memory */
+#define VEGAS_PIPE_ATOMS_F32 7 /* float atomic add to shared memory */
+#define VEGAS_PIPE_COUNT 8
+#define VEGAS_PIPE_SCRATCH_BYTES 64
+int vegas_pipe_peak(int op, uint32_t iters, void *d_scratch, size_t scratch_bytes,
+                    void *cuda_stream, double *out);
+
 /* Release the descriptor (not the caller's workspace).  Synchronises the
  * stream first.  NULL is accepted. */
 int vegas_destroy(vegas_state *s);

@@ -20,6 +20,9 @@ VEGAS_GAUSS, VEGAS_GAUSS_MIX2, VEGAS_FLAT, VEGAS_GENZ_DISC, VEGAS_GENZ_PPEAK, VE
 VEGAS_MAX_DIM, VEGAS_MAX_BINS, VEGAS_MAX_DIM_X_BINS = 20, 1024, 8192
 VEGAS_NOALLOC_MAX_DIM_X_BINS, VEGAS_NOALLOC_MAX_BLOCKS = 4096, 2048
 LOG_COLUMNS = ("S1", "S2", "n", "nonfinite", "I", "var")
+# vegas_pipe_peak operations, in the order of their VEGAS_PIPE_* codes
+PIPES = ("ffma", "dfma", "ex2", "product", "imad", "lds", "atoms_u32", "atoms_f32")
+VEGAS_PIPE_SCRATCH_BYTES = 64
 
 # every symbol include/vegas.h declares
 EXPORTED = ("vegas_workspace_bytes", "vegas_init_grid", "vegas_set_config", "vegas_iterate",
@@ -32,7 +35,7 @@ EXPORTED = ("vegas_workspace_bytes", "vegas_init_grid", "vegas_set_config", "veg
             "vegas_batch_destroy", "vegas_iterate_range", "vegas_shard_export",
             "vegas_shard_import", "vegas_export_state", "vegas_import_state",
             "vegas_set_user_integrand", "vegas_get_iteration_times",
-            "vegas_batch_set_tiles_by_dim", "vegas_set_box")
+            "vegas_batch_set_tiles_by_dim", "vegas_set_box", "vegas_pipe_peak")
 
 
 class VegasError(RuntimeError):
@@ -66,6 +69,8 @@ def lib():
                                       vp, sz, vp]
         L.vegas_set_config.argtypes = [vp, ctypes.POINTER(vegas_config)]
         L.vegas_set_box.argtypes = [vp, vp, vp]
+        L.vegas_pipe_peak.argtypes = [ctypes.c_int, ctypes.c_uint32, vp, ctypes.c_size_t, vp,
+                                      vp]
         L.vegas_iterate.argtypes = [vp, u64, i32]
         L.vegas_refine.argtypes = [vp, dbl]
         L.vegas_result.argtypes = [vp, i32, dp, dp, dp, ip]
@@ -138,6 +143,33 @@ def vegas_set_config(h, block_threads=0, blocks_per_sm=0, min_samples_per_thread
                      chunk_samples=0):
     cfg = vegas_config(block_threads, blocks_per_sm, min_samples_per_thread, chunk_samples)
     _check(lib().vegas_set_config(h, ctypes.byref(cfg)), "vegas_set_config")
+
+
+def vegas_pipe_peak(op, iters, d_scratch, scratch_bytes, cuda_stream):
+    """(lane-operations/s, SM MHz, SMs, blocks) of one VEGAS_PIPE_* operation."""
+    out = np.zeros(4)
+    _check(lib().vegas_pipe_peak(op, iters, d_scratch, scratch_bytes, cuda_stream,
+                                 out.ctypes.data), "vegas_pipe_peak")
+    return tuple(out)
+
+
+def pipe_peaks(pipes=PIPES, reps=2, device="cuda", stream=None):
+    """Measured peak of each named pipe on the current device: {name: {"per_s":
+    lane-operations/s (best of `reps` launches), "sm_mhz": the SM clock during
+    that launch, "per_sm_per_clk": per_s / (SMs x clock)}}."""
+    import torch
+
+    scratch = torch.zeros(VEGAS_PIPE_SCRATCH_BYTES, dtype=torch.uint8, device=device)
+    st = stream if stream is not None else torch.cuda.current_stream(scratch.device)
+    out = {}
+    for name in pipes:
+        best = max((vegas_pipe_peak(PIPES.index(name), 0, scratch.data_ptr(),
+                                    VEGAS_PIPE_SCRATCH_BYTES, st.cuda_stream)
+                    for _ in range(reps)), key=lambda r: r[0])
+        rate, mhz, sms, _ = best
+        out[name] = {"per_s": rate, "sm_mhz": mhz,
+                     "per_sm_per_clk": rate / (sms * mhz * 1e6) if mhz > 0 else None}
+    return out
 
 
 def vegas_set_box(h, box):
