@@ -102,9 +102,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="fp64,e2e,adjoint,batch,mix16,gauss20,genz16",
+    ap.add_argument("--legs", default="fp64,e2e,pipes,adjoint,batch,mix16,gauss20,genz16",
                     help="measurements besides the headline FP32 steps (comma list of "
-                         "fp64, e2e, adjoint, batch, mix16, gauss20, genz16; '' for none)")
+                         "fp64, e2e, pipes, adjoint, batch, mix16, gauss20, genz16; '' for none)")
     return ap.parse_args()
 
 
@@ -668,7 +668,7 @@ def main():
                 "binding_pipe": {"pipe": "fmaheavy: integer multiplies (34 Philox + 8 bin "
                                          "32x32->64 products per d=8 sample)",
                                  "busy_ncu": 0.735}}
-    if rank == 0:
+    if rank == 0 and "pipes" in legs:
         roofline["pipes"] = pipe_fractions(V, fixed_ms, statistics.median(adapt32_ns) / 1e6
                                            if adapt32_ns else None)
         roofline["frac_binding_pipe_measured"] = roofline["pipes"]["fixed_kernel"]["product"]["frac"]
