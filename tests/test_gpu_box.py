@@ -228,3 +228,28 @@ def test_checkpoint_carries_the_box(mode):
     assert np.allclose(b.grid(), a.grid(), rtol=0, atol=10 * tol)
     a.close()
     b.close()
+
+
+def test_virtual_ranks_over_a_box_equal_the_oracle():
+    """A boxed integral sharded over 3 virtual ranks (counter ranges, summed
+    partials, every rank refining) equals the oracle's boxed run (FP64)."""
+    from paper_2002_12921_b300.shard import GpuShardEngine, VirtualRanks
+
+    fid, dim, nbins, box, params = BOXES["gauss4"]
+    p = params()
+    sched = [(90_001, 1), (60_000, 1), (50_000, 0)]
+    states = []
+    for _ in range(3):
+        s = V.Vegas(dim, nbins, 13, V.VEGAS_FP64, fid, p, max_iters=8)
+        s.set_box(box)
+        states.append(s)
+    VirtualRanks([GpuShardEngine(s) for s in states]).run(sched)
+    o = oracle.run(dim, nbins, 13, fid, p, sched, nthreads=8, box=box)
+    for s in states:
+        rows = s.iterations()
+        for t, ref in enumerate(o["log"]):
+            tol = RTOL64 if t == 0 else fp64_tol(o["grids"][t])
+            assert abs(rows[t][4] - ref["I"]) <= tol * abs(ref["I"]), t
+        assert np.allclose(s.grid(), o["edges"], rtol=max(RTOL64, 2 * fp64_tol(o["grids"][1])),
+                           atol=1e-15)
+        s.close()
