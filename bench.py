@@ -102,9 +102,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="fp64,e2e,pipes,adjoint,batch,mix16,gauss20,genz16",
+    ap.add_argument("--legs", default="fp64,e2e,pipes,graph,adjoint,batch,mix16,gauss20,genz16",
                     help="measurements besides the headline FP32 steps (comma list of "
-                         "fp64, e2e, pipes, adjoint, batch, mix16, gauss20, genz16; '' for none)")
+                         "fp64, e2e, pipes, graph, adjoint, batch, mix16, gauss20, genz16; '' for none)")
     return ap.parse_args()
 
 
@@ -326,6 +326,41 @@ def adjoint_timing(V, stream, reps=3):
                      "samples": n, "I": float(o[0]), "dI_dmu": [float(x) for x in o[1:9]],
                      "dI_da": float(o[9]), "sigma_dI_da": float(o[19] ** 0.5)}
     return res
+
+
+def graph_timing(V, stream, reps=5):
+    """The d=8 step's schedule (10 x 1e7 adapting + 5 x 1e8 fixed, FP32) as one
+    CUDA graph replayed on a state, against the same schedule enqueued call by
+    call on an identical state (the paper's graph versus eager modes).  Both
+    states continue from their adapted grid after the first step, so both time
+    the same work; ms per step, median of `reps`."""
+    import torch
+
+    from paper_2002_12921_b300 import workloads as W
+
+    sched = [(N_ADAPT, 1)] * IT_ADAPT + [(N_FIXED, 0)] * IT_FIXED
+    iters = (reps + 1) * len(sched)
+    p = W.gauss_params(DIM, A)
+    stream = torch.cuda.Stream()  # CUDA captures only non-default streams
+    out = {}
+    for name in ("graph", "eager"):
+        v = V.Vegas(DIM, NBINS, 2, V.VEGAS_FP32_EVAL, V.VEGAS_GAUSS, p, max_iters=iters,
+                    stream=stream)
+        step = v.capture(sched).replay if name == "graph" else (lambda v=v: v.run(sched))
+        step()  # warm-up
+        ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        assert v.result(0)[3] == iters
+        v.close()
+        out[name + "_ms_per_step"] = statistics.median(ms)
+    out["launches_per_step"] = LAUNCHES_PER_STEP - 2  # the state's init and staging are not in it
+    return out
 
 
 def batch_timing(V, stream, reps=5):
@@ -679,6 +714,7 @@ def main():
         roofline["frac_at_measured_clock"] = achieved / (SMS * LANES_PER_SM * clk["sm_mhz"] * 1e6
                                                          / 1e12)
 
+    graph = graph_timing(V, stream) if rank == 0 and "graph" in legs else None
     adjoint = adjoint_timing(V, stream) if rank == 0 and "adjoint" in legs else None
     batch = batch_timing(V, stream) if rank == 0 and "batch" in legs else None
     mix16 = mix16_timing(V, stream) if rank == 0 and "mix16" in legs else None
@@ -722,6 +758,7 @@ def main():
             "speedup_fp32_over_fp64": value / fp64["value"] if fp64 else None,
             "adjoint_d8_a0.15_1e8": adjoint,
             "batch_256_gauss_8iters": batch,
+            "graph_vs_eager_d8_step": graph,
             "mix2_d16_N100_1e9_per_iter": mix16,
             "symgauss_d20_a0.1_N50_10x1e7adapt+5x1e8fixed": gauss20,
             "genz_d16_N50_10x1e7adapt+5x1e8fixed": genz16,

@@ -42,6 +42,17 @@
  *
  * Threads.  A state (or batch) is not thread-safe: calls on one state must not
  * run concurrently; different states may be used from different host threads.
+ *
+ * CUDA graphs.  vegas_iterate and vegas_refine only enqueue kernels (no host
+ * synchronisation), so a schedule of them can be captured from the state's
+ * stream into a CUDA graph.  The iteration number, the log row it fills and the
+ * float path's pre-scale are read from the state's device memory, not baked
+ * into the launch: every replay runs the captured schedule as further
+ * iterations (fresh Philox counters) from the grid it finds, appending to the
+ * log.  Replays do not advance the host's iteration count, so the log's
+ * capacity is enforced on the device: an iteration past max_iters does nothing
+ * and makes vegas_result return VEGAS_ESTATE.  vegas_set_box, vegas_shard_*
+ * and vegas_export_state rely on the host count; do not mix them with replays.
  */
 #ifndef VEGAS_B300_VEGAS_H
 #define VEGAS_B300_VEGAS_H

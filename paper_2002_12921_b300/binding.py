@@ -402,6 +402,21 @@ class Vegas:
             if adapt:
                 self.refine(alpha)
 
+    def capture(self, schedule, alpha=1.5):
+        """A CUDA graph of run(schedule), captured on this state's stream,
+        which must not be the default stream (nothing runs during the
+        capture).  Each replay() launches it on that stream and runs the
+        schedule as further iterations with fresh counters, from the grid it
+        finds; the log's capacity (max_iters) bounds the replays."""
+        import torch
+
+        if self.stream.cuda_stream == 0:
+            raise ValueError("capture needs a state created on a non-default stream")
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=self.stream):
+            self.run(schedule, alpha)
+        return StateGraph(graph, self.stream)
+
     def close(self):
         if self.handle:
             vegas_destroy(self.handle)
@@ -412,6 +427,20 @@ class Vegas:
             self.close()
         except Exception:
             pass
+
+
+class StateGraph:
+    """A captured schedule of one state (Vegas.capture); replay() launches it
+    on the state's stream."""
+
+    def __init__(self, graph, stream):
+        self.graph, self.stream = graph, stream
+
+    def replay(self):
+        import torch
+
+        with torch.cuda.stream(self.stream):
+            self.graph.replay()
 
 
 # ---------------------------------------------------------------- batches
