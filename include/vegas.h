@@ -155,7 +155,8 @@ int vegas_init_grid(vegas_state **out, int dim, int nbins, uint64_t seed, int mo
  * The integrand's parameters keep their meaning in x (e.g. the Gaussian's
  * centres and width); a caller-compiled integrand receives x.  Only before the
  * first iteration (else VEGAS_ESTATE); VEGAS_EINVAL on a bad box.  States with a
- * box are checkpointed with it; vegas_gauss_adjoint refuses them. */
+ * box are checkpointed with it, and vegas_gauss_adjoint differentiates the
+ * boxed integral. */
 int vegas_set_box(vegas_state *s, const double *lo, const double *hi);
 
 /* Change the launch configuration (cfg == NULL restores the defaults). */
@@ -252,8 +253,10 @@ int vegas_shard_import(vegas_state *s, const double *d_buf, uint64_t n_total);
  * I and its variance (the other entries are set to 0).  Uses the state's
  * mode, seed, grid, workspace and stream; the same (iter, n) as an earlier
  * vegas_iterate on the same grid reproduces its samples exactly.
- * Asynchronous.  The paper's integrator has no gradient; this is the
- * differentiable extension of the same estimator. */
+ * Over a box (vegas_set_box) the samples are x = lo + (hi - lo) u and this is
+ * the gradient of the boxed integral.  Asynchronous.  The paper's integrator
+ * has no gradient; this is the differentiable extension of the same
+ * estimator. */
 int vegas_gauss_adjoint(vegas_state *s, const double *params, int nparams, uint32_t iter,
                         uint64_t n_samples, int grad, double *d_out);
 

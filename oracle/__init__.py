@@ -56,6 +56,8 @@ def lib():
         L.oracle_combine.restype = None
         L.oracle_gauss_gradient.argtypes = [i32, i32, vp, u64, u32, u64, vp, vp]
         L.oracle_gauss_gradient.restype = i32
+        L.oracle_gauss_gradient_box.argtypes = [i32, i32, vp, u64, u32, u64, vp, vp, vp, vp]
+        L.oracle_gauss_gradient_box.restype = i32
         L.oracle_uniform_grid.argtypes = [i32, i32, vp]
         L.oracle_uniform_grid.restype = None
         _lib = L
@@ -196,15 +198,18 @@ def combine(I, var):
     return float(out[0]), float(out[1]), float(out[2])
 
 
-def gauss_gradient(edges, seed, it, n, params):
+def gauss_gradient(edges, seed, it, n, params, box=None):
     """Fixed-grid estimate of the Eq. 1 integral and its gradient in
     (mu_1..mu_d, a) over samples 0..n-1 of iteration it: dict(I, dmu, da,
-    var_I, var_dmu, var_da, nonfinite)."""
+    var_I, var_dmu, var_da, nonfinite).  box: [(lo_k, hi_k)] per dimension
+    (None: the unit cube)."""
     edges = _c(edges, np.float64)
     dim, nb1 = edges.shape
     p = _c(params, np.float64)
     out = np.zeros(2 * (dim + 2) + 1)
-    if lib().oracle_gauss_gradient(dim, nb1 - 1, _ptr(edges), seed, it, n, _ptr(p), _ptr(out)):
+    lo, w = _box(box, dim)
+    if lib().oracle_gauss_gradient_box(dim, nb1 - 1, _ptr(edges), seed, it, n, _ptr(p), _ptr(lo),
+                                       _ptr(w), _ptr(out)):
         raise ValueError("oracle_gauss_gradient: invalid arguments")
     nc = dim + 2
     return dict(I=out[0], dmu=out[1:dim + 1].copy(), da=out[dim + 1], var_I=out[nc],

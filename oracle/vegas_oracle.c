@@ -502,10 +502,12 @@ void oracle_integrand_batch(uint64_t n, int id, int dim, const double *params, c
 /*   df/dmu_k = f * 2 (x_k - mu_k) / a^2                                         */
 /*   df/da    = f * (2 sum_k (x_k - mu_k)^2 / a^3 - d / a)                        */
 /* params = [a, mu_1..mu_d].  out: [I, dI/dmu_1..dI/dmu_d, dI/da] then the      */
-/* variances of those d+2 sample means, then the non-finite count.              */
+/* variances of those d+2 sample means, then the non-finite count.  box_lo,     */
+/* box_w: the integration box as in oracle_iterate_range_box (NULL: unit cube). */
 /* ------------------------------------------------------------------------- */
-int oracle_gauss_gradient(int dim, int nbins, const double *edges, uint64_t seed, uint32_t iter,
-                          uint64_t n, const double *params, double *out)
+int oracle_gauss_gradient_box(int dim, int nbins, const double *edges, uint64_t seed,
+                              uint32_t iter, uint64_t n, const double *params,
+                              const double *box_lo, const double *box_w, double *out)
 {
     if (dim < 1 || dim > ORACLE_MAX_DIM || n < 2) return -1;
     const int nc = dim + 2;
@@ -522,6 +524,11 @@ int oracle_gauss_gradient(int dim, int nbins, const double *edges, uint64_t seed
         double J;
         oracle_sample_words(seed, 0, iter, i, dim, words);
         oracle_map_sample(dim, nbins, edges, words, x, &J, NULL);
+        if (box_lo) /* as in the iteration: x = lo + w u, J gains prod w */
+            for (int k = 0; k < dim; ++k) {
+                x[k] = box_lo[k] + box_w[k] * x[k];
+                J *= box_w[k];
+            }
         double fw = gauss_product(dim, a, mu, x) * J;
         if (!isfinite(fw)) { bad++; continue; }
         double sq = 0.0;
@@ -546,4 +553,10 @@ int oracle_gauss_gradient(int dim, int nbins, const double *edges, uint64_t seed
     out[2 * nc] = (double)bad;
     free(s1); free(s2); free(g);
     return 0;
+}
+
+int oracle_gauss_gradient(int dim, int nbins, const double *edges, uint64_t seed, uint32_t iter,
+                          uint64_t n, const double *params, double *out)
+{
+    return oracle_gauss_gradient_box(dim, nbins, edges, seed, iter, n, params, NULL, NULL, out);
 }

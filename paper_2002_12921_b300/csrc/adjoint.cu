@@ -180,11 +180,13 @@ extern "C" int vegas_gauss_adjoint(vegas_state* s, const double* params, int npa
     using namespace vegas;
     if (!s || !params || !d_out || nparams < 1 + s->dim) return VEGAS_EINVAL;
     if (n_samples < 2 || n_samples > (1ull << 40)) return VEGAS_EINVAL;
-    if (s->has_box) return VEGAS_EINVAL;  // derivatives are taken on the unit cube
     AdjointArgs a;
     std::memset(&a, 0, sizeof(a));
     if (make_consts(VEGAS_GAUSS, s->dim, s->nbins, params, nparams, &a.fc) != VEGAS_OK)
         return VEGAS_EINVAL;
+    // over a box the staged coordinate is still z = c (x - mu)/a with
+    // x = lo + w u, so the derivative formulas in z hold unchanged
+    if (s->has_box) compose_box(&a.fc, s->dim, s->box_lo, s->box_hi);
     const int dim = s->dim;
     const double width = params[0];
     // staged coordinate z = c (x - mu)/a: c = 1 (double), sqrt(log2 e) (float)

@@ -146,6 +146,19 @@ int make_consts(int integrand, int dim, int nbins, const double* params, int npa
     }
 }
 
+// The box composed into both precisions' staging: z = sc x + sh with
+// x = lo + w u becomes z = (sc w) u + (sc lo + sh); the staged widths then
+// carry w, so the Jacobian gains prod w with the prefactors unchanged.
+void compose_box(FnConsts* fc, int dim, const double* lo, const double* hi) {
+    for (int k = 0; k < dim; ++k) {
+        const double w = hi[k] - lo[k];
+        for (int p = 0; p < 2; ++p) {
+            fc->sh[p][k] = fc->sc[p][k] * lo[k] + fc->sh[p][k];
+            fc->sc[p][k] *= w;
+        }
+    }
+}
+
 // Inverse-variance combination of log rows first .. n-1 (columns I = 4,
 // var = 5; rows `stride` doubles apart).  An iteration with zero variance makes
 // the result the plain mean with sigma 0.  NaNs when there is no row.
@@ -453,18 +466,11 @@ int vegas_set_box(vegas_state* s, const double* lo, const double* hi) {
         w[k] = hi[k] - lo[k];
         if (!std::isfinite(w[k])) return VEGAS_EINVAL;
     }
-    // the integrand's constants afresh, then the box composed into both
-    // precisions' staging: z = sc x + sh with x = lo + w u becomes
-    // z = (sc w) u + (sc lo + sh); the staged widths then carry w, so the
-    // Jacobian gains prod w with the prefactors unchanged
+    // the integrand's constants afresh, then the box composed into them
     FnConsts fc;
     const int rc = make_consts(s->integrand, s->dim, s->nbins, s->params, s->nparams, &fc);
     if (rc != VEGAS_OK) return rc;
-    for (int k = 0; k < s->dim; ++k)
-        for (int p = 0; p < 2; ++p) {
-            fc.sh[p][k] = fc.sc[p][k] * lo[k] + fc.sh[p][k];
-            fc.sc[p][k] *= w[k];
-        }
+    compose_box(&fc, s->dim, lo, hi);
     fc.user = s->fc.user;
     s->fc = fc;
     s->has_box = 1;

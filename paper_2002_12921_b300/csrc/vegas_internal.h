@@ -77,6 +77,8 @@ struct FnConsts {
 // Fill FnConsts for an integrand (VEGAS_EINVAL on bad parameters).
 int make_consts(int integrand, int dim, int nbins, const double* params, int nparams,
                 FnConsts* fc);
+// Compose the integration box [lo_k, hi_k] into the staging of both precisions.
+void compose_box(FnConsts* fc, int dim, const double* lo, const double* hi);
 
 // Arguments of one iterate launch (passed by value in the parameter bank).
 struct IterArgs {

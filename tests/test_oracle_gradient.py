@@ -79,3 +79,86 @@ def test_closed_form_derivatives_by_differences():
         dn[k] -= h
         assert abs((closed_form(a, up)[0] - closed_form(a, dn)[0]) / (2 * h) - dmu[k]) < 1e-8
     assert abs((closed_form(a + h, mu)[0] - closed_form(a - h, mu)[0]) / (2 * h) - da) < 1e-8
+
+
+# ---------------------------------------------------------------- over a box
+BOX = [(-1.0, 1.0), (0.0, 2.5), (0.5, 1.0), (-3.0, -1.0)]
+MU_BOX = np.array([0.2, 1.1, 0.7, -2.2])
+
+
+def closed_form_box(a, mu, box):
+    """I = prod_k J_k over [lo_k, hi_k], J = (erf((hi-mu)/a) - erf((lo-mu)/a))/2:
+    dJ/dmu = (e^{-((lo-mu)/a)^2} - e^{-((hi-mu)/a)^2}) / (a sqrt(pi)),
+    dJ/da = -((hi-mu) e^{-((hi-mu)/a)^2} - (lo-mu) e^{-((lo-mu)/a)^2}) / (a^2 sqrt(pi))."""
+    lo, hi = np.array(box).T
+    u, v = (hi - mu) / a, (lo - mu) / a
+    J = 0.5 * (erf(u) - erf(v))
+    dJmu = (np.exp(-v * v) - np.exp(-u * u)) / (a * np.sqrt(np.pi))
+    dJa = -((hi - mu) * np.exp(-u * u) - (lo - mu) * np.exp(-v * v)) / (a * a * np.sqrt(np.pi))
+    others = np.array([np.prod(np.delete(J, k)) for k in range(len(mu))])
+    return np.prod(J), others * dJmu, float(np.sum(others * dJa))
+
+
+@pytest.fixture(scope="module")
+def box_grid():
+    p = W.gauss_params(4, 0.3, MU_BOX)
+    warm = oracle.run(4, 40, 6, W.GAUSS, p, [(100_000, 1)] * 4, nthreads=8, box=BOX)
+    return warm["edges"], p
+
+
+def test_closed_form_over_the_unit_box_is_the_unit_cube_one():
+    a, mu = 0.2, np.array([0.3, 0.55, 0.68])
+    for x, y in zip(closed_form_box(a, mu, [(0.0, 1.0)] * 3), closed_form(a, mu)):
+        assert np.allclose(x, y, rtol=1e-13, atol=0)
+
+
+def test_boxed_gradient_is_the_chain_rule_of_the_unit_cube_one(box_grid):
+    """A Gaussian (a, mu) over [lo, lo + w]^d is, sample for sample, the
+    unit-cube Gaussian (a/w, (mu - lo)/w): equal I, and every derivative is the
+    unit-cube one over w."""
+    e, _ = box_grid
+    lo, w, a = -0.4, 1.7, 0.35
+    mu = np.array([0.1, 0.5, 0.9, 0.3])
+    boxed = oracle.gauss_gradient(e, 4, 2, 30_000, W.gauss_params(4, a, mu),
+                                  box=[(lo, lo + w)] * 4)
+    unit = oracle.gauss_gradient(e, 4, 2, 30_000, W.gauss_params(4, a / w, (mu - lo) / w))
+    assert abs(boxed["I"] - unit["I"]) <= 1e-12 * abs(unit["I"])
+    assert np.allclose(boxed["dmu"], unit["dmu"] / w, rtol=1e-11, atol=0)
+    assert abs(boxed["da"] - unit["da"] / w) <= 1e-11 * abs(unit["da"])
+
+
+def test_boxed_gradient_matches_central_differences(box_grid):
+    e, p = box_grid
+    g = oracle.gauss_gradient(e, 6, 4, 20_000, p, box=BOX)
+    grad = np.concatenate([g["dmu"], [g["da"]]])
+    h, scale = 1e-4, np.max(np.abs(grad))
+    for c in range(5):
+        idx = 1 + c if c < 4 else 0
+        pp, pm = list(p), list(p)
+        pp[idx] += h
+        pm[idx] -= h
+        fd = (oracle.gauss_gradient(e, 6, 4, 20_000, pp, box=BOX)["I"] -
+              oracle.gauss_gradient(e, 6, 4, 20_000, pm, box=BOX)["I"]) / (2 * h)
+        assert abs(fd - grad[c]) <= 1e-6 * scale, (c, fd, grad[c])
+
+
+def test_boxed_gradient_agrees_with_erf_derivatives_over_the_box(box_grid):
+    e, p = box_grid
+    g = oracle.gauss_gradient(e, 6, 9, 400_000, p, box=BOX)
+    I, dmu, da = closed_form_box(p[0], MU_BOX, BOX)
+    assert abs(g["I"] - I) < 4 * np.sqrt(g["var_I"])
+    assert np.all(np.abs(g["dmu"] - dmu) < 4 * np.sqrt(g["var_dmu"]))
+    assert abs(g["da"] - da) < 4 * np.sqrt(g["var_da"])
+
+
+def test_boxed_closed_form_derivatives_by_differences():
+    a, h = 0.3, 1e-6
+    I, dmu, da = closed_form_box(a, MU_BOX, BOX)
+    for k in range(4):
+        up, dn = MU_BOX.copy(), MU_BOX.copy()
+        up[k] += h
+        dn[k] -= h
+        fd = (closed_form_box(a, up, BOX)[0] - closed_form_box(a, dn, BOX)[0]) / (2 * h)
+        assert abs(fd - dmu[k]) < 1e-8
+    fd = (closed_form_box(a + h, MU_BOX, BOX)[0] - closed_form_box(a - h, MU_BOX, BOX)[0]) / (2 * h)
+    assert abs(fd - da) < 1e-8
