@@ -430,6 +430,14 @@ int vegas_set_user_integrand(vegas_state *s, const vegas_user_integrand *u, cons
 int vegas_pipe_peak(int op, uint32_t iters, void *d_scratch, size_t scratch_bytes,
                     void *cuda_stream, double *out);
 
+/* ---- fault injection (testing) ------------------------------------------- */
+/* Make the countdown-th of this state's next enqueueing calls (vegas_iterate,
+ * vegas_iterate_range, vegas_refine; 1 = the next one) return VEGAS_ECUDA
+ * before it enqueues or changes anything, as a failed launch would, so that a
+ * caller's error handling and recovery can be tested without a GPU fault.
+ * countdown 0 cancels.  Host-side only.  VEGAS_EINVAL for countdown < 0. */
+int vegas_inject_failure(vegas_state *s, int countdown);
+
 /* Release the descriptor (not the caller's workspace).  Synchronises the
  * stream first.  NULL is accepted. */
 int vegas_destroy(vegas_state *s);

@@ -35,7 +35,8 @@ EXPORTED = ("vegas_workspace_bytes", "vegas_init_grid", "vegas_set_config", "veg
             "vegas_batch_destroy", "vegas_iterate_range", "vegas_shard_export",
             "vegas_shard_import", "vegas_export_state", "vegas_import_state",
             "vegas_set_user_integrand", "vegas_get_iteration_times",
-            "vegas_batch_set_tiles_by_dim", "vegas_set_box", "vegas_pipe_peak")
+            "vegas_batch_set_tiles_by_dim", "vegas_set_box", "vegas_pipe_peak",
+            "vegas_inject_failure")
 
 
 class VegasError(RuntimeError):
@@ -69,6 +70,7 @@ def lib():
                                       vp, sz, vp]
         L.vegas_set_config.argtypes = [vp, ctypes.POINTER(vegas_config)]
         L.vegas_set_box.argtypes = [vp, vp, vp]
+        L.vegas_inject_failure.argtypes = [vp, i32]
         L.vegas_pipe_peak.argtypes = [ctypes.c_int, ctypes.c_uint32, vp, ctypes.c_size_t, vp,
                                       vp]
         L.vegas_iterate.argtypes = [vp, u64, i32]
@@ -327,6 +329,11 @@ class Vegas:
         """Integrate over [(lo_k, hi_k)] instead of the unit cube (before the
         first iteration)."""
         vegas_set_box(self.handle, box)
+
+    def inject_failure(self, countdown):
+        """Testing hook: the countdown-th next iterate/refine call fails with
+        VEGAS_ECUDA before enqueueing anything (0 cancels)."""
+        _check(lib().vegas_inject_failure(self.handle, int(countdown)), "vegas_inject_failure")
 
     def set_user_integrand(self, desc, data=None, module=None):
         """Attach a VEGAS_USER_INTEGRAND descriptor (an address, e.g. from
@@ -602,6 +609,42 @@ def autotune(dim, nbins, mode, integrand, params, n, adapt=False, blocks=(128, 2
             v.close()
     bt, bps, ms = min(timings, key=timings.get)
     return dict(block_threads=bt, blocks_per_sm=bps, min_samples_per_thread=ms), timings
+
+
+class TuningTable:
+    """Tuned launch configurations kept in a JSON file, keyed by (mode,
+    integrand, dim, nbins, adapt, n bucket) -- the bucket is the power of ten
+    of the iteration's sample count -- so that a shape tuned once is not tuned
+    again in a later process.  lookup() returns the stored configuration or
+    runs `tuner` (autotune by default), stores and saves its choice."""
+
+    def __init__(self, path, tuner=None):
+        import json
+
+        self.path, self.tuner = path, tuner or autotune
+        self.entries = {}
+        if os.path.exists(path):
+            with open(path) as f:
+                self.entries = json.load(f)
+
+    @staticmethod
+    def key(mode, integrand, dim, nbins, n, adapt):
+        bucket = len(str(int(n))) - 1  # floor(log10 n)
+        return f"mode={mode},integrand={integrand},d={dim},N={nbins},adapt={int(bool(adapt))}," \
+               f"n=1e{bucket}"
+
+    def lookup(self, dim, nbins, mode, integrand, params, n, adapt=False, **tuner_kw):
+        import json
+
+        k = self.key(mode, integrand, dim, nbins, n, adapt)
+        if k not in self.entries:
+            cfg, _ = self.tuner(dim, nbins, mode, integrand, params, n, adapt=adapt, **tuner_kw)
+            self.entries[k] = {name: int(v) for name, v in cfg.items()}
+            tmp = self.path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(self.entries, f, indent=1, sort_keys=True)
+            os.replace(tmp, self.path)
+        return dict(self.entries[k])
 
 
 def autotune_batch(batch, blocks=(128, 256), tiles=(8192, 16384, 32768, 65536, 131072), reps=2,

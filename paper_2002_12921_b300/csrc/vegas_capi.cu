@@ -377,6 +377,7 @@ static int enqueue_iteration(vegas_state* s, uint64_t begin, uint64_t end, int a
     vegas::TraceRange trace_("vegas_iterate");
     const uint64_t n_samples = end - begin;
     if (s->host_iters >= s->max_iters) return VEGAS_ESTATE;
+    if (injected_failure(s)) return VEGAS_ECUDA;
     DeviceGuard g(s->device);
     if (!g.ok) return VEGAS_ECUDA;
 
@@ -483,6 +484,12 @@ int vegas_set_box(vegas_state* s, const double* lo, const double* hi) {
     return restage(s);
 }
 
+int vegas_inject_failure(vegas_state* s, int countdown) {
+    if (!s || countdown < 0) return VEGAS_EINVAL;
+    s->inject_countdown = countdown;
+    return VEGAS_OK;
+}
+
 int vegas_set_user_integrand(vegas_state* s, const vegas_user_integrand* u, const void* d_data) {
     if (!s || !u || s->integrand != VEGAS_USER || u->dim != s->dim ||
         u->args_bytes != sizeof(IterArgs) || !u->prepare || !u->launch)
@@ -535,6 +542,7 @@ int vegas_shard_import(vegas_state* s, const double* d_buf, uint64_t n_total) {
 int vegas_refine(vegas_state* s, double alpha) {
     vegas::TraceRange trace_("vegas_refine");
     if (!s || !(alpha >= 0.0) || !std::isfinite(alpha)) return VEGAS_EINVAL;
+    if (injected_failure(s)) return VEGAS_ECUDA;
     DeviceGuard g(s->device);
     if (!g.ok) return VEGAS_ECUDA;
     RefineArgs r{};

@@ -158,7 +158,14 @@ struct vegas_state {
     float2* staged32;  // VEGAS_FP32_EVAL: the grid's staged pairs in the workspace, else null
     int has_box;       // integration box [lo, hi] (vegas_set_box); else the unit cube
     double box_lo[VEGAS_MAX_DIM], box_hi[VEGAS_MAX_DIM];
+    int inject_countdown;  // vegas_inject_failure: fail the n-th next enqueueing call (0: off)
 };
+
+// vegas_inject_failure's check, at the start of every enqueueing call: true
+// when this call is the one to fail (nothing has been enqueued or changed).
+inline bool injected_failure(vegas_state* s) {
+    return s->inject_countdown > 0 && --s->inject_countdown == 0;
+}
 
 // Rewrite a float-path state's staged pairs after its edges changed other than
 // by vegas_refine (enqueued on the state's stream; VEGAS_OK for FP64 states).

@@ -38,9 +38,15 @@ class GpuShardEngine:
                                device=vegas.workspace.device)
 
     def iterate_range(self, n, begin, end, adapt):
-        self.B._check(self.B.lib().vegas_iterate_range(self.v.handle, int(n), int(begin),
-                                                       int(end), 1 if adapt else 0),
-                      "vegas_iterate_range")
+        rc = self.B.lib().vegas_iterate_range(self.v.handle, int(n), int(begin), int(end),
+                                              1 if adapt else 0)
+        if rc == self.B.VEGAS_ECUDA:
+            # a launch of this rank's range failed.  Run again, the range
+            # reproduces its samples exactly when the failure came before the
+            # first launch (an injected failure, a launch-configuration error);
+            # the iteration's log row and count are written only on success
+            raise RankFailure("vegas_iterate_range: " + self.B.lib().vegas_strerror(rc).decode())
+        self.B._check(rc, "vegas_iterate_range")
 
     def export(self):
         self.B._check(self.B.lib().vegas_shard_export(self.v.handle, self.buf.data_ptr()),

@@ -285,6 +285,23 @@ def test_autotuner_picks_a_candidate_that_keeps_results():
     assert rel(tuned["rows"][:, 4], base["rows"][:, 4]) < 1e-13
 
 
+def test_tuning_table_with_the_real_autotuner(tmp_path):
+    """TuningTable over the GPU autotuner: the stored choice is one of the
+    candidates, is reused from the file, and keeps results."""
+    p = W.gauss_params(5, 0.15)
+    path = str(tmp_path / "tuning.json")
+    kw = dict(blocks=(128, 256), blocks_per_sm=(0,), min_samples=(8,), reps=1)
+    cfg = V.binding.TuningTable(path).lookup(5, 30, V.VEGAS_FP64, W.GAUSS, p, 300_007, True,
+                                             **kw)
+    assert cfg["block_threads"] in (128, 256)
+    again = V.binding.TuningTable(path, tuner=lambda *a, **k: pytest.fail("re-tuned"))
+    assert again.lookup(5, 30, V.VEGAS_FP64, W.GAUSS, p, 300_007, True) == cfg
+    sched = [(300_007, 1), (300_007, 0)]
+    base = gpu_run(5, 30, 3, W.GAUSS, p, sched, V.VEGAS_FP64)
+    tuned = gpu_run(5, 30, 3, W.GAUSS, p, sched, V.VEGAS_FP64, cfg=cfg)
+    assert rel(tuned["rows"][:, 4], base["rows"][:, 4]) < 1e-13
+
+
 def test_iteration_device_times_match_cuda_events():
     """vegas_get_iteration_times: each iteration's device time is positive, no
     longer than the CUDA-event time around its launches and most of it; a

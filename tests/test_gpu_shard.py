@@ -62,3 +62,32 @@ def test_gpu_virtual_ranks_fp32_match_one_state_and_survive_a_failure():
         assert np.allclose(s.grid(), one.grid(), rtol=0, atol=1e-6)
         s.close()
     one.close()
+
+
+def test_a_failed_launch_is_retried_and_the_run_stays_exact():
+    """A rank whose range launch fails (vegas_inject_failure: VEGAS_ECUDA
+    before anything is enqueued) is re-run by the coordinator; the result
+    equals the oracle's, and a state's own next call after a failure works."""
+    states = [V.Vegas(6, 40, 21, V.VEGAS_FP64, W.GAUSS, P, max_iters=8) for _ in range(2)]
+    states[1].inject_failure(3)  # its third enqueueing call: iteration 1's range
+    vr = VirtualRanks([GpuShardEngine(s) for s in states])
+    vr.run(SCHED)
+    assert [(f[0], f[1]) for f in vr.failures] == [(1, 1)]
+    ref = oracle.run(6, 40, 21, W.GAUSS, P, SCHED, nthreads=8)
+    for s in states:
+        rows = s.iterations()
+        for t, r in enumerate(ref["log"]):
+            tol = 1e-12 if t == 0 else fp64_tol(ref["grids"][t])
+            assert abs(rows[t][4] - r["I"]) <= tol * abs(r["I"]), t
+        s.close()
+    v = V.Vegas(3, 10, 1, V.VEGAS_FP32_EVAL, W.GAUSS, W.gauss_params(3, 0.2), max_iters=4)
+    v.inject_failure(1)
+    with pytest.raises(V.VegasError) as e:
+        v.iterate(10_000, 1)
+    assert e.value.status == V.VEGAS_ECUDA
+    v.inject_failure(1)
+    with pytest.raises(V.VegasError):
+        v.refine()
+    v.run([(10_000, 1), (10_000, 0)])  # the state is untouched and usable
+    assert v.result(0)[3] == 2
+    v.close()
