@@ -1,5 +1,5 @@
 // Instantiates the fused iterate kernel for double arithmetic and the VEGAS_GENZ_PPEAK
-// integrand, dimensions 1..16, with and without the refinement histogram.
+// integrand, dimensions 1..20, with and without the refinement histogram.
 #include "iterate_kernel.cuh"
 
 VEGAS_KERNEL_TABLE(iterate_table_f64_genz_ppeak, double, VEGAS_GENZ_PPEAK)
