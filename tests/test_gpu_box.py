@@ -276,3 +276,30 @@ def test_adjoint_over_a_box_matches_the_oracle(mode, tol):
         sg = np.sqrt(np.concatenate([[o["var_I"]], o["var_dmu"], [o["var_da"]]]))
         assert np.all(np.abs(out[:6] - og) <= tol * sg)
     assert out[12] == 0
+
+
+@pytest.mark.parametrize("dim,nbins,box", [
+    (20, 50, [(-0.5 - 0.05 * k, 1.0 + 0.1 * k) for k in range(20)]),   # the largest dimension
+    (3, 1, [(2.0, 5.0), (-1.0, 0.0), (0.0, 0.125)]),                  # one bin: plain MC
+    (2, 40, [(1e3, 1e3 + 1e-3), (-7.5, -7.25)]),                       # narrow, far from 0
+])
+def test_fp64_boxed_edge_cases_match_oracle(dim, nbins, box):
+    lo, hi = np.array(box).T
+    p = W.gauss_params(dim, 0.5, (lo + hi) / 2 + 0.1 * (hi - lo))
+    if dim == 2:
+        p = W.gauss_params(dim, 1e-3, (lo + hi) / 2)
+    sched = [(20_011, 1), (20_011, 1), (10_000, 0)]
+    rows, grids, edges = boxed_run(dim, nbins, 33, W.GAUSS, p, box, sched, V.VEGAS_FP64)
+    o = oracle.run(dim, nbins, 33, W.GAUSS, p, sched, nthreads=8, box=box)
+    for t, ref in enumerate(o["log"]):
+        tol = RTOL64 if t == 0 else fp64_tol(o["grids"][t])
+        if dim == 2:
+            # x = lo + w u near 1e3 carries eps |x| of rounding on either side,
+            # which z = (x - mu)/a magnifies by 1/a: f = e^{-z^2} moves by
+            # 2 |z| dz relative, and samples with |z| > 6 carry less than
+            # e^-36 of I, so the bound is sum_k 4 * 6 eps |x_k|max / a, with
+            # no averaging over samples assumed
+            xmax = np.maximum(np.abs(lo), np.abs(hi))
+            tol = max(tol, np.sum(24 * np.finfo(float).eps * xmax / p[0]))
+        assert abs(rows[t][4] - ref["I"]) <= tol * abs(ref["I"]), (t, rows[t][4], ref["I"])
+    assert np.all(np.diff(edges, axis=1) > 0)
