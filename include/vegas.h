@@ -286,6 +286,19 @@ int vegas_batch_workspace_bytes(int count, const int *dims, const uint64_t *n_sa
 int vegas_batch_init(vegas_batch **out, int count, const int *dims, const uint64_t *n_samples,
                      int nbins, uint64_t seed, int mode, const double *params, int max_iters,
                      void *d_workspace, size_t ws_bytes, void *cuda_stream);
+/* The same for any built-in integrand (VEGAS_GAUSS .. VEGAS_GENZ_PPEAK, shared
+ * by the batch; VEGAS_EINVAL for VEGAS_USER): params holds each integral's
+ * parameters in that integrand's layout (VEGAS_GAUSS 1 + d, VEGAS_GAUSS_MIX2
+ * 1 + 2d, VEGAS_GENZ_* 2d, VEGAS_FLAT none; params may be NULL when the total
+ * is 0), concatenated in order.  box_lo, box_hi: NULL for the unit cube, else
+ * each integral's box [lo_k, hi_k] (as vegas_set_box), dims[b] doubles per
+ * integral concatenated in order (sum_b dims[b] each).  vegas_batch_init is
+ * this call with VEGAS_GAUSS and no box. */
+int vegas_batch_init_integrand(vegas_batch **out, int count, const int *dims,
+                               const uint64_t *n_samples, int nbins, uint64_t seed, int mode,
+                               int integrand, const double *params, const double *box_lo,
+                               const double *box_hi, int max_iters, void *d_workspace,
+                               size_t ws_bytes, void *cuda_stream);
 /* Block size (32..256, multiple of 32) and samples per tile (>= 4096, multiple
  * of 32); 0 keeps the current value.  Rebuilds the tile table. */
 int vegas_batch_set_config(vegas_batch *b, int block_threads, uint64_t tile_samples);

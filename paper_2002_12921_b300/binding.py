@@ -36,7 +36,7 @@ EXPORTED = ("vegas_workspace_bytes", "vegas_init_grid", "vegas_set_config", "veg
             "vegas_shard_import", "vegas_export_state", "vegas_import_state",
             "vegas_set_user_integrand", "vegas_get_iteration_times",
             "vegas_batch_set_tiles_by_dim", "vegas_set_box", "vegas_pipe_peak",
-            "vegas_inject_failure")
+            "vegas_inject_failure", "vegas_batch_init_integrand")
 
 
 class VegasError(RuntimeError):
@@ -89,6 +89,8 @@ def lib():
         L.vegas_batch_workspace_bytes.argtypes = [i32, vp, vp, i32, i32, ctypes.POINTER(sz)]
         L.vegas_batch_init.argtypes = [ctypes.POINTER(vp), i32, vp, vp, i32, u64, i32, vp, i32,
                                        vp, sz, vp]
+        L.vegas_batch_init_integrand.argtypes = [ctypes.POINTER(vp), i32, vp, vp, i32, u64, i32,
+                                                 i32, vp, vp, vp, i32, vp, sz, vp]
         L.vegas_batch_set_config.argtypes = [vp, i32, u64]
         L.vegas_batch_set_tiles_by_dim.argtypes = [vp, vp, i32]
         L.vegas_batch_set_stream.argtypes = [vp, vp]
@@ -469,22 +471,35 @@ def vegas_batch_workspace_bytes(dims, n_samples, nbins, max_iters):
 
 
 def vegas_batch_init(dims, n_samples, nbins, seed, mode, params_list, max_iters, d_workspace,
-                     ws_bytes, cuda_stream):
-    dims_a, n_a, flat = _batch_arrays(dims, n_samples, params_list)
+                     ws_bytes, cuda_stream, integrand=VEGAS_GAUSS, boxes=None):
+    """A batch handle.  integrand: one built-in id for every integral;
+    params_list: each integral's parameters in that integrand's layout;
+    boxes: None, or each integral's [(lo_k, hi_k)] (None entries: unit cube)."""
+    dims_a, n_a, flat = _batch_arrays(dims, n_samples, [p if p is not None else []
+                                                        for p in params_list])
+    lo = hi = None
+    if boxes is not None:
+        rows = [np.asarray(bx if bx is not None else [(0.0, 1.0)] * d, dtype=np.float64)
+                .reshape(d, 2) for bx, d in zip(boxes, dims_a)]
+        both = np.concatenate(rows)
+        lo, hi = np.ascontiguousarray(both[:, 0]), np.ascontiguousarray(both[:, 1])
     h = ctypes.c_void_p(None)
-    _check(lib().vegas_batch_init(ctypes.byref(h), len(dims_a), dims_a.ctypes.data,
-                                  n_a.ctypes.data, nbins, seed & (2**64 - 1), mode,
-                                  flat.ctypes.data, max_iters, d_workspace, ws_bytes,
-                                  cuda_stream), "vegas_batch_init")
+    _check(lib().vegas_batch_init_integrand(
+        ctypes.byref(h), len(dims_a), dims_a.ctypes.data, n_a.ctypes.data, nbins,
+        seed & (2**64 - 1), mode, integrand, flat.ctypes.data if flat.size else None,
+        lo.ctypes.data if lo is not None else None, hi.ctypes.data if hi is not None else None,
+        max_iters, d_workspace, ws_bytes, cuda_stream), "vegas_batch_init_integrand")
     return h.value
 
 
 class VegasBatch:
-    """Many Eq. 1 Gaussian integrals advanced together (one persistent launch
-    per iteration); torch owns the workspace and supplies the stream."""
+    """Many integrals of one built-in integrand family (default: the Eq. 1
+    Gaussian) advanced together, one persistent launch per iteration, each over
+    the unit cube or its own box; torch owns the workspace and supplies the
+    stream."""
 
     def __init__(self, dims, n_samples, nbins, seed, mode, params_list, max_iters=16,
-                 device="cuda", stream=None):
+                 device="cuda", stream=None, integrand=VEGAS_GAUSS, boxes=None):
         import torch
 
         self.dims = [int(d) for d in dims]
@@ -495,7 +510,7 @@ class VegasBatch:
             self.workspace.device)
         self.handle = vegas_batch_init(self.dims, n_samples, nbins, seed, mode, params_list,
                                        max_iters, self.workspace.data_ptr(), self.ws_bytes,
-                                       self.stream.cuda_stream)
+                                       self.stream.cuda_stream, integrand, boxes)
 
     def config(self, block_threads=0, tile_samples=0):
         _check(lib().vegas_batch_set_config(self.handle, block_threads, tile_samples),

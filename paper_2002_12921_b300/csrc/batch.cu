@@ -158,7 +158,7 @@ BatchLayout batch_layout(int count, const int* dims, const uint64_t* n, int nbin
 using namespace vegas;
 
 struct vegas_batch {
-    int count, nbins, mode, max_iters;
+    int count, nbins, mode, integrand, max_iters;
     uint64_t seed;
     cudaStream_t stream;
     int device, sm_count;
@@ -180,6 +180,18 @@ struct vegas_batch {
 };
 
 namespace {
+
+// Parameters of one integral of dimension d for a built-in integrand (the
+// layouts of include/vegas.h).
+int batch_nparams(int integrand, int d) {
+    switch (integrand) {
+    case VEGAS_GAUSS: return 1 + d;
+    case VEGAS_GAUSS_MIX2: return 1 + 2 * d;
+    case VEGAS_GENZ_DISC:
+    case VEGAS_GENZ_PPEAK: return 2 * d;
+    default: return 0;
+    }
+}
 
 struct Dev {
     int prev = -1;
@@ -259,14 +271,29 @@ int vegas_batch_workspace_bytes(int count, const int* dims, const uint64_t* n_sa
     return VEGAS_OK;
 }
 
-int vegas_batch_init(vegas_batch** out, int count, const int* dims, const uint64_t* n_samples,
-                     int nbins, uint64_t seed, int mode, const double* params, int max_iters,
-                     void* d_workspace, size_t ws_bytes, void* cuda_stream) {
+int vegas_batch_init_integrand(vegas_batch** out, int count, const int* dims,
+                               const uint64_t* n_samples, int nbins, uint64_t seed, int mode,
+                               int integrand, const double* params, const double* box_lo,
+                               const double* box_hi, int max_iters, void* d_workspace,
+                               size_t ws_bytes, void* cuda_stream) {
     if (!out) return VEGAS_EINVAL;
     *out = nullptr;
-    if (!batch_shape_ok(count, dims, n_samples, nbins, max_iters) || !params || !d_workspace)
+    if (!batch_shape_ok(count, dims, n_samples, nbins, max_iters) || !d_workspace)
         return VEGAS_EINVAL;
     if (mode != VEGAS_FP64 && mode != VEGAS_FP32_EVAL) return VEGAS_EINVAL;
+    if (!batch_iterate_kernel_f64(integrand, false)) return VEGAS_EINVAL;  // built-in only
+    if ((box_lo == nullptr) != (box_hi == nullptr)) return VEGAS_EINVAL;
+    size_t total_params = 0, total_dims = 0;
+    for (int i = 0; i < count; ++i) {
+        total_params += batch_nparams(integrand, dims[i]);
+        total_dims += dims[i];
+    }
+    if (total_params > 0 && !params) return VEGAS_EINVAL;
+    if (box_lo)
+        for (size_t k = 0; k < total_dims; ++k)
+            if (!std::isfinite(box_lo[k]) || !std::isfinite(box_hi[k]) ||
+                !(box_hi[k] > box_lo[k]) || !std::isfinite(box_hi[k] - box_lo[k]))
+                return VEGAS_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_workspace) % kAlign) return VEGAS_EINVAL;
     const BatchLayout L = batch_layout(count, dims, n_samples, nbins, max_iters);
     if (ws_bytes < L.total) return VEGAS_ENOSPACE;
@@ -281,6 +308,7 @@ int vegas_batch_init(vegas_batch** out, int count, const int* dims, const uint64
     b->count = count;
     b->nbins = nbins;
     b->mode = mode;
+    b->integrand = integrand;
     b->max_iters = max_iters;
     b->seed = seed;
     b->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -297,14 +325,17 @@ int vegas_batch_init(vegas_batch** out, int count, const int* dims, const uint64
     b->consts.resize(count);
     b->info.resize(count);
     b->max_dim = 0;
-    size_t eoff = 0, hoff = 0, p = 0;
+    size_t eoff = 0, hoff = 0, p = 0, boff = 0;
     for (int i = 0; i < count; ++i) {
-        if (make_consts(VEGAS_GAUSS, dims[i], nbins, params + p, 1 + dims[i], &b->consts[i]) !=
-            VEGAS_OK) {
+        const int np = batch_nparams(integrand, dims[i]);
+        if (make_consts(integrand, dims[i], nbins, np ? params + p : nullptr, np,
+                        &b->consts[i]) != VEGAS_OK) {
             delete b;
             return VEGAS_EINVAL;
         }
-        p += 1 + dims[i];
+        if (box_lo) compose_box(&b->consts[i], dims[i], box_lo + boff, box_hi + boff);
+        p += np;
+        boff += dims[i];
         b->info[i].dim = dims[i];
         b->info[i].pad = 0;
         b->info[i].n = n_samples[i];
@@ -340,6 +371,15 @@ int vegas_batch_init(vegas_batch** out, int count, const int* dims, const uint64
     }
     *out = b;
     return VEGAS_OK;
+}
+
+int vegas_batch_init(vegas_batch** out, int count, const int* dims, const uint64_t* n_samples,
+                     int nbins, uint64_t seed, int mode, const double* params, int max_iters,
+                     void* d_workspace, size_t ws_bytes, void* cuda_stream) {
+    if (!params) return VEGAS_EINVAL;
+    return vegas_batch_init_integrand(out, count, dims, n_samples, nbins, seed, mode,
+                                      VEGAS_GAUSS, params, nullptr, nullptr, max_iters,
+                                      d_workspace, ws_bytes, cuda_stream);
 }
 
 int vegas_batch_set_config(vegas_batch* b, int block_threads, uint64_t tile_samples) {
@@ -415,8 +455,8 @@ int vegas_batch_iterate(vegas_batch* b, int adapt, double alpha) {
     std::memcpy(a.rk0, b->rk0, sizeof(a.rk0));
     std::memcpy(a.rk1, b->rk1, sizeof(a.rk1));
 
-    const void* kern = b->mode == VEGAS_FP32_EVAL ? batch_iterate_kernel_f32(ad)
-                                                  : batch_iterate_kernel_f64(ad);
+    const void* kern = b->mode == VEGAS_FP32_EVAL ? batch_iterate_kernel_f32(b->integrand, ad)
+                                                  : batch_iterate_kernel_f64(b->integrand, ad);
     const size_t smem = iterate_smem_bytes(b->mode, b->max_dim, b->nbins, ad, a.hist_log2r);
     if (smem > 40 * 1024 &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=

@@ -1,9 +1,22 @@
-// Instantiates the batch iterate kernel for float arithmetic.
+// The batch iterate kernels for float arithmetic, by integrand (one
+// instantiation file per integrand: batch_f32_*.cu).
 #include "batch_kernel.cuh"
 
 namespace vegas {
-const void* batch_iterate_kernel_f32(bool adapt) {
-    return adapt ? (const void*)&batch_iterate_kernel<float, true>
-                 : (const void*)&batch_iterate_kernel<float, false>;
+const void* batch_table_f32_gauss(bool adapt);
+const void* batch_table_f32_mix2(bool adapt);
+const void* batch_table_f32_flat(bool adapt);
+const void* batch_table_f32_genz_disc(bool adapt);
+const void* batch_table_f32_genz_ppeak(bool adapt);
+
+const void* batch_iterate_kernel_f32(int integrand, bool adapt) {
+    switch (integrand) {
+    case VEGAS_GAUSS: return batch_table_f32_gauss(adapt);
+    case VEGAS_GAUSS_MIX2: return batch_table_f32_mix2(adapt);
+    case VEGAS_FLAT: return batch_table_f32_flat(adapt);
+    case VEGAS_GENZ_DISC: return batch_table_f32_genz_disc(adapt);
+    case VEGAS_GENZ_PPEAK: return batch_table_f32_genz_ppeak(adapt);
+    default: return nullptr;
+    }
 }
 }  // namespace vegas

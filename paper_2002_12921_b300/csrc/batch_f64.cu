@@ -1,9 +1,22 @@
-// Instantiates the batch iterate kernel for double arithmetic.
+// The batch iterate kernels for double arithmetic, by integrand (one
+// instantiation file per integrand: batch_f64_*.cu).
 #include "batch_kernel.cuh"
 
 namespace vegas {
-const void* batch_iterate_kernel_f64(bool adapt) {
-    return adapt ? (const void*)&batch_iterate_kernel<double, true>
-                 : (const void*)&batch_iterate_kernel<double, false>;
+const void* batch_table_f64_gauss(bool adapt);
+const void* batch_table_f64_mix2(bool adapt);
+const void* batch_table_f64_flat(bool adapt);
+const void* batch_table_f64_genz_disc(bool adapt);
+const void* batch_table_f64_genz_ppeak(bool adapt);
+
+const void* batch_iterate_kernel_f64(int integrand, bool adapt) {
+    switch (integrand) {
+    case VEGAS_GAUSS: return batch_table_f64_gauss(adapt);
+    case VEGAS_GAUSS_MIX2: return batch_table_f64_mix2(adapt);
+    case VEGAS_FLAT: return batch_table_f64_flat(adapt);
+    case VEGAS_GENZ_DISC: return batch_table_f64_genz_disc(adapt);
+    case VEGAS_GENZ_PPEAK: return batch_table_f64_genz_ppeak(adapt);
+    default: return nullptr;
+    }
 }
 }  // namespace vegas

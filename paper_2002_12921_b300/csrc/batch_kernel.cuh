@@ -5,7 +5,9 @@
 // the next tile index from an atomic ticket -- there is no waiting on other
 // blocks -- stages that integral's grid in shared memory, runs the shared
 // sample loop (integral_id = b in the Philox counter) and adds the tile's
-// sums and histogram to integral b's accumulators with FP64 atomics.  A
+// sums and histogram to integral b's accumulators with FP64 atomics.  The
+// batch's integrals share one built-in integrand (a template parameter), each
+// with its own parameters and box in its FnConsts.  A
 // second, small launch refines every (integral, dimension) row and records
 // each integral's estimate (batch.cu).
 #pragma once
@@ -46,8 +48,8 @@ struct BatchArgs {
     unsigned rk0[10], rk1[10];
 };
 
-// One tile of integral b with compile-time dimension D.
-template <typename R, int D, bool ADAPT>
+// One tile of integral b with compile-time dimension D and integrand FN.
+template <typename R, int D, int FN, bool ADAPT>
 __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchTile& t,
                                            typename Prec<R>::Pair* sgrid,
                                            typename Prec<R>::Hist* shist, double* sred,
@@ -71,7 +73,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchTile& 
     __syncthreads();
 
     IterateSink<R, D, ADAPT> sink(shist, N, logr);
-    bool checks_ok = sample_loop<R, D, Integrand<R, VEGAS_GAUSS>>(
+    bool checks_ok = sample_loop<R, D, Integrand<R, FN>>(
         t.start + threadIdx.x, t.start + t.count, blockDim.x, a.iter, t.b << 8, a.rk0, a.rk1,
         fc, N, (R)(sizeof(R) == 4 ? fc.C32 : fc.C), n4, nlast, sgrid, sink);
 #ifdef VEGAS_DEBUG_CHECKS
@@ -95,7 +97,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchTile& 
     __syncthreads();  // the next tile restages the shared memory
 }
 
-template <typename R, bool ADAPT>
+template <typename R, int FN, bool ADAPT>
 __global__ void __launch_bounds__(256) batch_iterate_kernel(const BatchArgs a) {
     using P = Prec<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(256) batch_iterate_kernel(const BatchArgs a) {
         const BatchTile t = a.tiles[ti];
         switch (a.info[t.b].dim) {
 #define VEGAS_BATCH_CASE(D) \
-    case D: batch_tile<R, D, ADAPT>(a, t, sgrid, shist, sred, sbad); break;
+    case D: batch_tile<R, D, FN, ADAPT>(a, t, sgrid, shist, sred, sbad); break;
             VEGAS_BATCH_CASE(1) VEGAS_BATCH_CASE(2) VEGAS_BATCH_CASE(3) VEGAS_BATCH_CASE(4)
             VEGAS_BATCH_CASE(5) VEGAS_BATCH_CASE(6) VEGAS_BATCH_CASE(7) VEGAS_BATCH_CASE(8)
             VEGAS_BATCH_CASE(9) VEGAS_BATCH_CASE(10) VEGAS_BATCH_CASE(11) VEGAS_BATCH_CASE(12)
@@ -125,9 +127,19 @@ __global__ void __launch_bounds__(256) batch_iterate_kernel(const BatchArgs a) {
     }
 }
 
-// the batch iterate kernel of a precision, for the host (defined in
-// batch_f32.cu / batch_f64.cu)
-const void* batch_iterate_kernel_f32(bool adapt);
-const void* batch_iterate_kernel_f64(bool adapt);
+// the batch iterate kernel of a precision and built-in integrand, for the
+// host (batch_f32.cu / batch_f64.cu; nullptr for an integrand it lacks)
+const void* batch_iterate_kernel_f32(int integrand, bool adapt);
+const void* batch_iterate_kernel_f64(int integrand, bool adapt);
 
 }  // namespace vegas
+
+// One (precision, integrand) pair's kernels, both adapt flags, as the
+// function NAME(adapt) (one source file each, so that they compile in parallel).
+#define VEGAS_BATCH_TABLE(NAME, R, FN)                                          \
+    namespace vegas {                                                           \
+    const void* NAME(bool adapt) {                                              \
+        return adapt ? (const void*)&batch_iterate_kernel<R, FN, true>          \
+                     : (const void*)&batch_iterate_kernel<R, FN, false>;        \
+    }                                                                           \
+    }

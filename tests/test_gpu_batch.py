@@ -208,3 +208,69 @@ def test_full_batch_of_256():
                            for b, p in enumerate(params))
     assert within[V.VEGAS_FP64] >= 230
     assert within[V.VEGAS_FP32_EVAL] >= within[V.VEGAS_FP64] - 3
+
+
+# ------------------------------------------- other integrands and boxes
+def family_batch(fid):
+    """Four integrals of one family, uneven dimension and sample count; the
+    second and fourth over boxes (the rest on the unit cube)."""
+    dims = [2, 5, 3, 7]
+    ns = [20_011, 15_000, 9_999, 12_000]
+    if fid == W.GAUSS_MIX2:
+        params = [W.mix2_params(d, 0.2) for d in dims]
+    elif fid == W.FLAT:
+        params = [[] for _ in dims]
+    else:
+        params = [W.genz_params(d, seed=10 + d, kind=fid) for d in dims]
+    boxes = [None, [(-1.0, 2.0)] * 5, None, [(0.25 * k, 0.25 * k + 1.5) for k in range(7)]]
+    return dims, ns, params, boxes
+
+
+@pytest.mark.parametrize("fid", [W.GAUSS_MIX2, W.FLAT, W.GENZ_DISC, W.GENZ_PPEAK])
+def test_batch_of_any_builtin_integrand_matches_the_oracle(fid):
+    """FP64: every integral of a batch of the family equals the oracle's run
+    with its integral id and box, iteration by iteration, and its final grid."""
+    dims, ns, params, boxes = family_batch(fid)
+    B = V.VegasBatch(dims, ns, 25, 17, V.VEGAS_FP64, params, max_iters=6, integrand=fid,
+                     boxes=boxes)
+    B.config(tile_samples=4096)
+    B.reset()
+    for t in range(4):
+        B.iterate(adapt=t < 3)
+    log = B.log()
+    for b, (d, n, p, box) in enumerate(zip(dims, ns, params, boxes)):
+        o = oracle.run(d, 25, 17, fid, p, [(n, 1)] * 3 + [(n, 0)], integral_id=b, nthreads=4,
+                       box=box)
+        for t in range(4):
+            tol = 1e-12 if t == 0 else fp64_tol(o["grids"][t])
+            I = o["log"][t]["I"]
+            assert log[b, t, 2] == n
+            assert abs(log[b, t, 4] - I) <= tol * abs(I) + 1e-300, (fid, b, t, log[b, t, 4], I)
+        assert np.allclose(B.grid(b), o["edges"], rtol=max(1e-12, 2 * fp64_tol(o["grids"][2])),
+                           atol=1e-15)
+    B.close()
+
+
+def test_fp32_boxed_mixture_batch_first_iteration_within_float_bound():
+    dims, ns, params, boxes = family_batch(W.GAUSS_MIX2)
+    B = V.VegasBatch(dims, ns, 25, 17, V.VEGAS_FP32_EVAL, params, max_iters=4,
+                     integrand=W.GAUSS_MIX2, boxes=boxes)
+    B.reset()
+    B.iterate(adapt=True)
+    log = B.log()
+    for b, (d, n, p, box) in enumerate(zip(dims, ns, params, boxes)):
+        o = oracle.iterate(oracle.uniform_grid(d, 25), 17, 0, n, W.GAUSS_MIX2, p, True,
+                           integral_id=b, box=box)
+        assert abs(log[b, 0, 4] - o["I"]) <= 1e-5 * abs(o["I"]), b
+    B.close()
+
+
+def test_batch_init_refuses_bad_integrands_and_boxes():
+    dims, ns = [2, 3], [5000, 5000]
+    with pytest.raises(V.VegasError) as e:  # no caller-compiled integrands in a batch
+        V.VegasBatch(dims, ns, 10, 1, V.VEGAS_FP64, [[], []], integrand=V.VEGAS_USER)
+    assert e.value.status == V.VEGAS_EINVAL
+    with pytest.raises(V.VegasError) as e:  # an empty interval
+        V.VegasBatch(dims, ns, 10, 1, V.VEGAS_FP64, [[], []], integrand=W.FLAT,
+                     boxes=[None, [(0.0, 1.0), (1.0, 1.0), (0.0, 1.0)]])
+    assert e.value.status == V.VEGAS_EINVAL
