@@ -438,6 +438,28 @@ class Vegas:
             pass
 
 
+def integrate(integrand, params, dim, n_iter, n_events, adapt_iters=None, nbins=50,
+              mode=VEGAS_FP32_EVAL, seed=1, alpha=1.5, box=None, stream=None):
+    """One call from integrand to result, the shape of the paper's wrapper
+    (integrand, dimension, iterations, events per iteration): n_iter
+    iterations of n_events samples, of which the first adapt_iters (default:
+    all but the last, at least one) adapt the grid; returns (mean, sigma,
+    chi2_dof) combined over the iterations on the frozen grid, or over all of
+    them when every iteration adapts."""
+    if n_iter < 1:
+        raise ValueError("n_iter must be >= 1")
+    k = max(1, n_iter - 1) if adapt_iters is None else int(adapt_iters)
+    v = Vegas(dim, nbins, seed, mode, integrand, params, max_iters=n_iter, stream=stream)
+    try:
+        if box is not None:
+            v.set_box(box)
+        v.run([(n_events, 1)] * k + [(n_events, 0)] * (n_iter - k), alpha)
+        mean, sigma, chi2, _, _ = v.result(k if k < n_iter else 0)
+    finally:
+        v.close()
+    return mean, sigma, chi2
+
+
 class StateGraph:
     """A captured schedule of one state (Vegas.capture); replay() launches it
     on the state's stream."""

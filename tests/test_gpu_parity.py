@@ -7,6 +7,8 @@ FP32-eval mode: compared on the same grid and counters within the float
 error budget (|dI| <= 1e-5 |I|, |dvar| <= 1e-4 var for d <= 8; 3x that at
 d = 16), and statistically (3 sigma) over whole runs.
 """
+import math
+
 import numpy as np
 import pytest
 from scipy.special import erf
@@ -300,6 +302,30 @@ def test_tuning_table_with_the_real_autotuner(tmp_path):
     base = gpu_run(5, 30, 3, W.GAUSS, p, sched, V.VEGAS_FP64)
     tuned = gpu_run(5, 30, 3, W.GAUSS, p, sched, V.VEGAS_FP64, cfg=cfg)
     assert rel(tuned["rows"][:, 4], base["rows"][:, 4]) < 1e-13
+
+
+def test_one_call_integrate_equals_the_state_run_and_the_closed_form():
+    p = W.gauss_params(4, 0.1)
+    m, s, c = V.binding.integrate(V.VEGAS_GAUSS, p, 4, n_iter=6, n_events=200_000,
+                                  mode=V.VEGAS_FP64, seed=5)
+    g = gpu_run(4, 50, 5, W.GAUSS, p, [(200_000, 1)] * 5 + [(200_000, 0)], V.VEGAS_FP64,
+                first_iter=5)
+    assert abs(m - g["result"][0]) <= 1e-13 * abs(m)
+    assert abs(m - math.erf(5.0) ** 4) < 5 * s
+    # f = 1 over a box of volume 12 on the fixed uniform grid: f J is the volume
+    # (FP64: exact to rounding; FP32-eval's sigma has a floor near
+    # I sqrt(eps_f / n), the float rounding of every (f J)^2 alike)
+    box = [(0.0, 2.0), (1.0, 4.0), (-1.0, 1.0)]
+    mb, sb, _ = V.binding.integrate(V.VEGAS_FLAT, [], 3, n_iter=2, n_events=10_000,
+                                    adapt_iters=0, box=box, mode=V.VEGAS_FP64)
+    assert abs(mb - 12.0) < 1e-13 * 12 and sb < 1e-12
+    mf, sf, _ = V.binding.integrate(V.VEGAS_FLAT, [], 3, n_iter=2, n_events=10_000,
+                                    adapt_iters=0, box=box)
+    assert abs(mf - 12.0) < 1e-6 * 12 and sf < 12 * 4 * math.sqrt(2.0 ** -23 / 20_000)
+    # adapting to a flat integrand follows the histogram's sampling noise, so
+    # the grid moves and the later estimate is only statistically exact
+    ma, sa, _ = V.binding.integrate(V.VEGAS_FLAT, [], 3, n_iter=3, n_events=10_000, box=box)
+    assert abs(ma - 12.0) < 5 * sa
 
 
 def test_iteration_device_times_match_cuda_events():
