@@ -261,9 +261,11 @@ int vegas_gauss_adjoint(vegas_state *s, const double *params, int nparams, uint3
                         uint64_t n_samples, int grad, double *d_out);
 
 /* ---- many integrals in one persistent launch ------------------------------ */
-/* A batch holds `count` independent Eq. 1 Gaussian integrals (VegasFlow
- * Sec. 3.1) of their own dimension (1..20) and samples per iteration, all with
- * nbins bins per dimension, sharing one seed and one iteration schedule.
+/* A batch holds `count` independent integrals of one built-in integrand family
+ * (Eq. 1 Gaussians with vegas_batch_init; any family, and a box per integral,
+ * with vegas_batch_init_integrand), each of its own dimension (1..20), samples
+ * per iteration and parameters, all with nbins bins per dimension, sharing one
+ * seed and one iteration schedule.
  * Integral b draws its samples with integral_id = b in the counter (see the
  * top of this file), so its result equals that of a single vegas_state run
  * with the same grid, seed and iteration indices and integral id b.
