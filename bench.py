@@ -84,6 +84,28 @@ def pipe_fractions(V, fixed_ms, adapt_ms):
     return out
 
 
+def add_product_fractions(peak, adjoint, batch, mix16, gauss20, genz16):
+    """Each FP32 leg's rate of 32x32 -> 64-bit products (the binding pipe of
+    every float kernel) as a fraction of the measured product peak, written
+    into the leg's fp32 record as product_frac_of_measured."""
+    def put(rec, products_per_s):
+        rec["product_frac_of_measured"] = products_per_s / peak
+
+    if adjoint:
+        for k in ("forward_ms", "backward_ms"):
+            adjoint["fp32"]["product_frac_" + k[:-3] + "_of_measured"] = (
+                products_per_sample(8) * adjoint["fp32"]["samples"] / (adjoint["fp32"][k] / 1e3)
+                / peak)
+    if batch:
+        put(batch["fp32"], batch["products_per_run"] / (batch["fp32"]["graph_ms"] / 1e3))
+    for leg, d in ((mix16, 16), (gauss20, 20)):
+        if leg:
+            put(leg["fp32"], products_per_sample(d) * leg["fp32"]["samples_per_s"])
+    if genz16:
+        for fam in genz16.values():
+            put(fam["fp32"], products_per_sample(16) * fam["fp32"]["samples_per_s"])
+
+
 def alg_ops_per_sample(d):
     """Algorithmic lane-operations of one FP32 fixed-grid sample: Philox (10
     rounds x 2 wide multiplies + 2 three-input xors per call), per dimension
@@ -389,7 +411,8 @@ def batch_timing(V, stream, reps=5):
     ns = [w.schedule[0][0] for w in wls]
     params = [w.params for w in wls]
     total = 8 * sum(ns)
-    res = {"integrals": len(wls), "iterations": 8, "samples_per_run": total}
+    res = {"integrals": len(wls), "iterations": 8, "samples_per_run": total,
+           "products_per_run": 8 * sum(n * products_per_sample(d) for d, n in zip(dims, ns))}
     for name, mode in (("fp32", V.VEGAS_FP32_EVAL), ("fp64", V.VEGAS_FP64)):
         B = V.VegasBatch(dims, ns, 50, wls[0].seed, mode, params, max_iters=8, stream=stream)
         choice, _ = V.binding.autotune_batch(B, reps=1)
@@ -750,6 +773,10 @@ def main():
         cb = cpu_baseline()
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu_model",
                                   "single_core", "mix16")}
+
+    if rank == 0 and roofline.get("pipes"):
+        add_product_fractions(roofline["pipes"]["measured"]["product"]["per_s"], adjoint, batch,
+                              mix16, gauss20, genz16)
 
     if rank == 0:
         m32, s32 = res32[0], res32[1]
