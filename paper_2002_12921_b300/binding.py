@@ -177,7 +177,8 @@ def pipe_peaks(pipes=PIPES, reps=2, device="cuda", stream=None):
 
 
 def vegas_set_box(h, box):
-    """box: [(lo_k, hi_k)] per dimension."""
+    """box: [(lo_k, hi_k)] for each of the state's dimensions (the C call reads
+    exactly dim of each; Vegas.set_box checks the shape)."""
     b = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(-1, 2))
     lo, hi = np.ascontiguousarray(b[:, 0]), np.ascontiguousarray(b[:, 1])
     _check(lib().vegas_set_box(h, lo.ctypes.data, hi.ctypes.data), "vegas_set_box")
@@ -226,6 +227,8 @@ def vegas_get_grid(h, dim, nbins):
 
 
 def vegas_set_grid(h, edges):
+    """edges: dim x (nbins + 1) doubles (the C call reads exactly that many;
+    Vegas.set_grid checks the shape)."""
     e = np.ascontiguousarray(edges, dtype=np.float64)
     _check(lib().vegas_set_grid(h, e.ctypes.data), "vegas_set_grid")
 
@@ -330,7 +333,10 @@ class Vegas:
     def set_box(self, box):
         """Integrate over [(lo_k, hi_k)] instead of the unit cube (before the
         first iteration)."""
-        vegas_set_box(self.handle, box)
+        b = np.asarray(box, dtype=np.float64)
+        if b.shape != (self.dim, 2):
+            raise ValueError(f"box must be {self.dim} (lo, hi) pairs, got shape {b.shape}")
+        vegas_set_box(self.handle, b)
 
     def inject_failure(self, countdown):
         """Testing hook: the countdown-th next iterate/refine call fails with
@@ -388,7 +394,10 @@ class Vegas:
         return vegas_get_grid(self.handle, self.dim, self.nbins)
 
     def set_grid(self, edges):
-        vegas_set_grid(self.handle, edges)
+        e = np.asarray(edges, dtype=np.float64)
+        if e.shape != (self.dim, self.nbins + 1):
+            raise ValueError(f"edges must have shape {(self.dim, self.nbins + 1)}, got {e.shape}")
+        vegas_set_grid(self.handle, e)
 
     def histogram(self):
         return vegas_get_histogram(self.handle, self.dim, self.nbins)
@@ -497,8 +506,16 @@ def vegas_batch_init(dims, n_samples, nbins, seed, mode, params_list, max_iters,
     """A batch handle.  integrand: one built-in id for every integral;
     params_list: each integral's parameters in that integrand's layout;
     boxes: None, or each integral's [(lo_k, hi_k)] (None entries: unit cube)."""
-    dims_a, n_a, flat = _batch_arrays(dims, n_samples, [p if p is not None else []
-                                                        for p in params_list])
+    params_list = [p if p is not None else [] for p in params_list]
+    if len(params_list) != len(dims) or (boxes is not None and len(boxes) != len(dims)):
+        raise ValueError("need one parameter list (and one box, if any) per integral")
+    for d, p in zip(dims, params_list):  # the C call reads exactly these counts
+        need = {VEGAS_GAUSS: 1 + d, VEGAS_GAUSS_MIX2: 1 + 2 * d, VEGAS_GENZ_DISC: 2 * d,
+                VEGAS_GENZ_PPEAK: 2 * d}.get(integrand, 0)
+        if len(p) != need:
+            raise ValueError(f"integrand {integrand} in dimension {d} takes {need} "
+                             f"parameters, got {len(p)}")
+    dims_a, n_a, flat = _batch_arrays(dims, n_samples, params_list)
     lo = hi = None
     if boxes is not None:
         rows = [np.asarray(bx if bx is not None else [(0.0, 1.0)] * d, dtype=np.float64)
