@@ -54,6 +54,11 @@ class GpuShardEngine:
         return self.buf
 
     def import_(self, totals, n):
+        # the library reads exactly 3 + dim * nbins doubles of device memory
+        if (totals.numel() != self.buf.numel() or totals.dtype != self.buf.dtype
+                or totals.device != self.buf.device or not totals.is_contiguous()):
+            raise ValueError(f"totals must be a contiguous float64 tensor of "
+                             f"{self.buf.numel()} elements on {self.buf.device}")
         self.B._check(self.B.lib().vegas_shard_import(self.v.handle, totals.data_ptr(), int(n)),
                       "vegas_shard_import")
 
