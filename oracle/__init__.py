@@ -23,7 +23,9 @@ def lib():
     """Load (building if needed) the oracle shared library."""
     global _lib
     if _lib is None:
-        path = _build()
+        # VEGAS_ORACLE_LIBRARY: another build of the oracle (the test suite's
+        # planted-mistake check points it at altered copies)
+        path = os.environ.get("VEGAS_ORACLE_LIBRARY") or _build()
         L = ctypes.CDLL(path)
         u64, i32, u32, dbl = ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, ctypes.c_double
         vp = ctypes.c_void_p

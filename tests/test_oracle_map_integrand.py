@@ -99,6 +99,19 @@ def test_gauss_integrand_2d_and_mixture():
     assert abs(valm - expect) < 1e-9
 
 
+def test_mixture_with_asymmetric_centres_by_quadrature():
+    """Centres whose components differ (the symmetric (1/3, 2/3) pair above
+    would not tell the two centres' coordinates apart): the quadrature of the
+    mixture equals the mean of the two erf closed forms."""
+    a, mu_a, mu_b = 0.15, [0.2, 0.7], [0.6, 0.35]
+    p = [a] + mu_a + mu_b
+    val, _ = integrate.dblquad(lambda y, x: oracle.integrand(W.GAUSS_MIX2, p,
+                                                             np.array([[x, y]]))[0],
+                               0, 1, 0, 1, epsabs=1e-12, epsrel=1e-11)
+    expect = 0.5 * (gauss_closed(a, mu_a) + gauss_closed(a, mu_b))
+    assert abs(val - expect) < 1e-9
+
+
 @pytest.mark.parametrize("kind", [W.GENZ_DISC, W.GENZ_PPEAK])
 @pytest.mark.parametrize("dim", [1, 2])
 def test_genz_integrands_integrate_to_one(kind, dim):

@@ -100,6 +100,20 @@ def test_refine_against_independent_construction(alpha):
     assert np.allclose(got[0, 1:-1], expect, rtol=0, atol=1e-12)
 
 
+def test_refine_tie_at_a_zero_weight_plateau_goes_to_the_lower_bin():
+    """N = 8, histogram (0, 1, 0, 0, 0, 0, 1, 0) on the uniform grid: the
+    smoothed row is symmetric with zero weight in bins 3 and 4, so the
+    cumulative weight equals half the total on the whole plateau [3/8, 5/8]
+    and the middle target 4 (total / 8) meets it exactly.  With ties going to
+    the lower bin (the reading of the re-partition rule), the middle edge is the
+    plateau's lower end, 3/8; the edges stay symmetric about 1/2 otherwise."""
+    e0 = np.linspace(0.0, 1.0, 9)[None, :]
+    h = np.array([[0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.0]])
+    e = oracle.refine(e0, h, 1.5)[0]
+    assert e[4] == 0.375
+    assert np.allclose(e[1:4], 1.0 - e[7:4:-1], rtol=0, atol=1e-15)
+
+
 def test_refine_one_hot_concentrates():
     """P6: all interior edges move into the hot bin and its two neighbours."""
     N = 50
