@@ -79,6 +79,23 @@ MUTANTS = [
     ("gradient in a", "g[dim + 1] = fw * (2.0 * sq / (a * a * a) - dim / a);",
      "g[dim + 1] = fw * (2.0 * sq / (a * a * a) + dim / a);"),
     ("gradient box Jacobian", "                J *= box_w[k];", "                J *= 1.0;"),
+    ("gradient variance sums", "s2[c] += (long double)g[c] * g[c];",
+     "s2[c] += (long double)g[c];"),
+    # more corners
+    ("counter without the high word", "ctr[1] = (uint32_t)(i >> 32);", "ctr[1] = 0;"),
+    ("Genz discontinuous normalisation", "norm *= (exp(c[k]) - exp(c[k] * a[k])) / c[k];",
+     "norm *= (exp(c[k]) - exp(a[k])) / c[k];"),
+    ("Genz product-peak normalisation", "atan(c[k] * (1.0 - a[k])) + atan(c[k] * a[k])",
+     "atan(c[k] * (1.0 - a[k])) + atan(a[k])"),
+    ("mixture without the half", "return 0.5 * (gauss_product(dim, params[0], params + 1, x) +",
+     "return 1.0 * (gauss_product(dim, params[0], params + 1, x) +"),
+    ("estimate divisor", "*I = S1 / nn;", "*I = S1 / (nn - 1.0);"),
+    ("smoothing far end", "out[N - 1] = (hist[N - 2] + hist[N - 1]) / 2.0;",
+     "out[N - 1] = (hist[N - 2] + hist[N - 1]) / 3.0;"),
+    ("overlapping thread slices",
+     "jb->end = first + (uint64_t)(((unsigned __int128)n * (uint64_t)(t + 1)) / (uint64_t)nthreads);",
+     "jb->end = first + (uint64_t)(((unsigned __int128)n * (uint64_t)(t + 1)) / (uint64_t)nthreads)"
+     " + (t + 1 < nthreads);"),
 ]
 
 
