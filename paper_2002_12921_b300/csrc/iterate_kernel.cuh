@@ -643,9 +643,14 @@ __device__ __forceinline__ void iterate_body(const IterArgs& a) {
     }
 }
 
-// The built-in integrands' kernel.
-template <typename R, int D, int FN, bool ADAPT>
-__global__ void VEGAS_ITERATE_BOUNDS vegas_iterate_kernel(const IterArgs a) {
+// The built-in integrands' kernel.  BIG: the instantiation for one block of
+// up to kBigBlockThreads per SM (float adapting iterations whose 32
+// lane-owned histogram copies fit that block's shared memory but not the
+// default budget); its own launch bound leaves the default kernels' register
+// allocation as it is.
+template <typename R, int D, int FN, bool ADAPT, bool BIG = false>
+__global__ void __launch_bounds__(BIG ? kBigBlockThreads : 256)
+    vegas_iterate_kernel(const IterArgs a) {
     iterate_body<R, D, Integrand<R, FN>, ADAPT>(a);
 }
 
@@ -664,6 +669,22 @@ __global__ void VEGAS_ITERATE_BOUNDS vegas_user_iterate_kernel(const IterArgs a)
 #define VEGAS_KERNEL_ROW(R, FN, D) \
     {(const void*)&vegas::vegas_iterate_kernel<R, D, FN, false>, \
      (const void*)&vegas::vegas_iterate_kernel<R, D, FN, true>}
+
+// The big-block adapting kernels of one float integrand: index [dim - 1].
+#define VEGAS_KERNEL_TABLE_BIG(name, FN)                                                     \
+    namespace vegas {                                                                         \
+    const void* name(int dim) {                                                               \
+        static const void* const table[kMaxDim] = {                                           \
+            VEGAS_BIG(FN, 1),  VEGAS_BIG(FN, 2),  VEGAS_BIG(FN, 3),  VEGAS_BIG(FN, 4),          \
+            VEGAS_BIG(FN, 5),  VEGAS_BIG(FN, 6),  VEGAS_BIG(FN, 7),  VEGAS_BIG(FN, 8),          \
+            VEGAS_BIG(FN, 9),  VEGAS_BIG(FN, 10), VEGAS_BIG(FN, 11), VEGAS_BIG(FN, 12),         \
+            VEGAS_BIG(FN, 13), VEGAS_BIG(FN, 14), VEGAS_BIG(FN, 15), VEGAS_BIG(FN, 16),         \
+            VEGAS_BIG(FN, 17), VEGAS_BIG(FN, 18), VEGAS_BIG(FN, 19), VEGAS_BIG(FN, 20)};        \
+        if (dim < 1 || dim > kMaxDim) return nullptr;                                         \
+        return table[dim - 1];                                                                \
+    }                                                                                         \
+    }
+#define VEGAS_BIG(FN, D) (const void*)&vegas::vegas_iterate_kernel<float, D, FN, true, true>
 
 #define VEGAS_KERNEL_TABLE(name, R, FN)                                                       \
     namespace vegas {                                                                         \

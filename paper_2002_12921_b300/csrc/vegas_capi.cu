@@ -33,6 +33,23 @@ const void* iterate_kernel_f32(int integrand, int dim, bool adapt) {
     }
 }
 
+const void* iterate_table_big_f32_gauss(int dim);
+const void* iterate_table_big_f32_mix2(int dim);
+const void* iterate_table_big_f32_flat(int dim);
+const void* iterate_table_big_f32_genz_disc(int dim);
+const void* iterate_table_big_f32_genz_ppeak(int dim);
+
+const void* iterate_kernel_f32_big(int integrand, int dim) {
+    switch (integrand) {
+    case VEGAS_GAUSS: return iterate_table_big_f32_gauss(dim);
+    case VEGAS_GAUSS_MIX2: return iterate_table_big_f32_mix2(dim);
+    case VEGAS_FLAT: return iterate_table_big_f32_flat(dim);
+    case VEGAS_GENZ_DISC: return iterate_table_big_f32_genz_disc(dim);
+    case VEGAS_GENZ_PPEAK: return iterate_table_big_f32_genz_ppeak(dim);
+    default: return nullptr;
+    }
+}
+
 const void* iterate_kernel_f64(int integrand, int dim, bool adapt) {
     switch (integrand) {
     case VEGAS_GAUSS: return iterate_table_f64_gauss(dim, adapt);
@@ -331,11 +348,17 @@ int vegas_init_grid(vegas_state** out, int dim, int nbins, uint64_t seed, int mo
 
     DeviceGuard g(s->device);
     if (!g.ok) { delete s; return VEGAS_ECUDA; }
+    int optin = 0;
     if (cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device) !=
-        cudaSuccess) {
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device) !=
+            cudaSuccess) {
         delete s;
         return VEGAS_ECUDA;
     }
+    // dynamic shared memory a block may take, less what the kernels declare
+    // statically (reductions and the tile index, under 1 KB)
+    s->smem_optin = optin > 1024 ? optin - 1024 : 0;
     s->ws = static_cast<unsigned char*>(d_workspace);
     s->ws_bytes = ws_bytes;
     s->edges = reinterpret_cast<double*>(s->ws + L.edges);
@@ -384,11 +407,24 @@ static int enqueue_iteration(vegas_state* s, uint64_t begin, uint64_t end, int a
     const bool ad = adapt != 0;
     const bool user = s->integrand == VEGAS_USER;
     if (user && !s->user.launch) return VEGAS_ESTATE;
-    const void* kern = user ? nullptr : kernel_for(s, ad);
+    const void* kern = user ? nullptr : kernel_for(s, ad);  // the big-block shape may replace it
     if (!user && !kern) return VEGAS_EINVAL;
-    const int log2r = ad ? hist_log2r(s->mode, s->dim, s->nbins) : 0;
+    int log2r = ad ? hist_log2r(s->mode, s->dim, s->nbins) : 0;
+    int block = s->cfg.block_threads;
+    // A float adapting iteration whose 32 lane-owned histogram copies miss the
+    // default budget runs as one big block per SM when they fit its shared
+    // memory: no two lanes of a warp then share a copy (no retried
+    // compare-and-swap adds, no bank conflicts) at the same occupancy.  Only
+    // under the default launch configuration.
+    if (ad && !user && s->mode == VEGAS_FP32_EVAL && log2r < 5 && s->cfg.block_threads == 256 &&
+        s->cfg.blocks_per_sm == 0 &&
+        iterate_smem_bytes(s->mode, s->dim, s->nbins, true, 5) <= (size_t)s->smem_optin &&
+        iterate_kernel_f32_big(s->integrand, s->dim)) {
+        log2r = 5;
+        block = kBigBlockThreads;
+        kern = iterate_kernel_f32_big(s->integrand, s->dim);
+    }
     const size_t smem = iterate_smem_bytes(s->mode, s->dim, s->nbins, ad, log2r);
-    const int block = s->cfg.block_threads;
     int occ = 0;
     if (user) {
         if (s->user.prepare(s->mode, ad ? 1 : 0, block, smem, &occ) != 0 || occ < 1)

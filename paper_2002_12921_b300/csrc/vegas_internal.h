@@ -111,10 +111,15 @@ struct RefineArgs {
 // Kernel lookup: the iterate kernel for (mode, integrand, dim, adapt), or
 // nullptr.
 const void* iterate_kernel_f32(int integrand, int dim, bool adapt);
+// The float big-block adapting kernel (kBigBlockThreads threads per block).
+const void* iterate_kernel_f32_big(int integrand, int dim);
 const void* iterate_kernel_f64(int integrand, int dim, bool adapt);
 // Shared histogram copies of an adapting iterate block, as log2: 32 copies
 // (one per lane) where they fit in kHistCopyBudget bytes, fewer otherwise.
 constexpr size_t kHistCopyBudget = 52 * 1024;
+// The big-block shape of a float adapting launch: one block of this many
+// threads per SM (24 warps, the occupancy of the default shape), 32 copies.
+constexpr int kBigBlockThreads = 768;
 int hist_log2r(int mode, int dim, int nbins);
 // dynamic shared memory of an iterate kernel with 2^log2r histogram copies
 size_t iterate_smem_bytes(int mode, int dim, int nbins, bool adapt, int log2r);
@@ -159,6 +164,7 @@ struct vegas_state {
     int has_box;       // integration box [lo, hi] (vegas_set_box); else the unit cube
     double box_lo[VEGAS_MAX_DIM], box_hi[VEGAS_MAX_DIM];
     int inject_countdown;  // vegas_inject_failure: fail the n-th next enqueueing call (0: off)
+    int smem_optin;        // dynamic shared memory one block may use on this device
 };
 
 // vegas_inject_failure's check, at the start of every enqueueing call: true

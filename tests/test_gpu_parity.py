@@ -287,6 +287,32 @@ def test_autotuner_picks_a_candidate_that_keeps_results():
     assert rel(tuned["rows"][:, 4], base["rows"][:, 4]) < 1e-13
 
 
+@pytest.mark.parametrize("fid,dim,nbins", [(W.GAUSS_MIX2, 16, 100), (W.GAUSS, 20, 50),
+                                            (W.GENZ_PPEAK, 12, 64)])
+def test_big_block_adapting_shape_equals_the_default_shape(fid, dim, nbins):
+    """Float adapting iterations whose 32 lane-owned histogram copies miss the
+    default budget run as one 768-thread block per SM; forcing the default
+    shape (blocks_per_sm set) gives the same sums and histogram up to float
+    summation order, and the same samples (the counters)."""
+    if fid == W.GAUSS_MIX2:
+        p = W.mix2_params(dim, 0.1)
+    elif fid == W.GAUSS:
+        p = W.gauss_params(dim, 0.1)
+    else:
+        p = W.genz_params(dim, seed=dim, kind=fid)
+    out = []
+    for cfg in ({}, {"blocks_per_sm": 1}):
+        v = V.Vegas(dim, nbins, 5, V.VEGAS_FP32_EVAL, fid, p, max_iters=4)
+        v.config(**cfg)
+        v.iterate(1_000_003, 1)
+        out.append((v.iterations()[0], v.histogram()))
+        v.close()
+    (rb, hb), (rd, hd) = out
+    assert rb[2] == rd[2] and rb[3] == rd[3]
+    assert abs(rb[4] - rd[4]) <= 1e-6 * abs(rd[4])
+    assert np.allclose(hb, hd, rtol=1e-5, atol=1e-30 * np.max(hd))
+
+
 def test_tuning_table_with_the_real_autotuner(tmp_path):
     """TuningTable over the GPU autotuner: the stored choice is one of the
     candidates, is reused from the file, and keeps results."""
