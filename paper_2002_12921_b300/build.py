@@ -74,6 +74,10 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False) -> st
     extra = ("-DVEGAS_DEBUG_CHECKS",) if debug else ()
     os.makedirs(out_dir, exist_ok=True)
     srcs = sources()
+    # a library newer than every source and header is current, whether or not
+    # its object files are at hand (a copy of the tree may carry only the .so)
+    if not force and not _stale(lib, srcs + headers()):
+        return lib
     if force:
         for o in glob.glob(os.path.join(out_dir, "*.o")):
             os.remove(o)

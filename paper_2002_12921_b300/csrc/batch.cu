@@ -162,6 +162,7 @@ struct vegas_batch {
     uint64_t seed;
     cudaStream_t stream;
     int device, sm_count;
+    int smem_optin;  // dynamic shared memory one block may use on this device
     unsigned char* ws;
     BatchLayout L;
     int max_dim;
@@ -348,10 +349,14 @@ int vegas_batch_init_integrand(vegas_batch** out, int count, const int* dims,
     }
     Dev g(b->device);
     int rc = g.ok ? VEGAS_OK : VEGAS_ECUDA;
+    int optin = 0;
     if (rc == VEGAS_OK &&
-        cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device) !=
-            cudaSuccess)
+        (cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device) !=
+             cudaSuccess ||
+         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) !=
+             cudaSuccess))
         rc = VEGAS_ECUDA;
+    b->smem_optin = optin > 1024 ? optin - 1024 : 0;  // less the kernels' static shared
     if (rc == VEGAS_OK &&
         (cudaMemcpyAsync(at<FnConsts>(b, L.consts), b->consts.data(), count * sizeof(FnConsts),
                          cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
@@ -457,20 +462,31 @@ int vegas_batch_iterate(vegas_batch* b, int adapt, double alpha) {
 
     const void* kern = b->mode == VEGAS_FP32_EVAL ? batch_iterate_kernel_f32(b->integrand, ad)
                                                   : batch_iterate_kernel_f64(b->integrand, ad);
+    int block = b->block_threads;
+    // float adapting rounds whose 32 copies for the widest integral miss the
+    // default budget run as one big block per SM when they fit it (as the
+    // single-integral kernels do), at the default block size only
+    if (ad && b->mode == VEGAS_FP32_EVAL && a.hist_log2r < 5 && block == 256 &&
+        iterate_smem_bytes(b->mode, b->max_dim, b->nbins, true, 5) <= (size_t)b->smem_optin &&
+        batch_iterate_kernel_f32_big(b->integrand)) {
+        a.hist_log2r = 5;
+        block = kBigBlockThreads;
+        kern = batch_iterate_kernel_f32_big(b->integrand);
+    }
     const size_t smem = iterate_smem_bytes(b->mode, b->max_dim, b->nbins, ad, a.hist_log2r);
     if (smem > 40 * 1024 &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
         return VEGAS_ECUDA;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, b->block_threads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) !=
             cudaSuccess ||
         occ < 1)
         return VEGAS_ECUDA;
     long long grid = (long long)b->sm_count * occ;
     if (grid > (long long)b->num_tiles) grid = b->num_tiles;
     void* args[] = {&a};
-    if (cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(b->block_threads), args, smem,
+    if (cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(block), args, smem,
                          b->stream) != cudaSuccess)
         return VEGAS_ECUDA;
 

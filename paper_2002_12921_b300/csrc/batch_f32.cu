@@ -19,4 +19,20 @@ const void* batch_iterate_kernel_f32(int integrand, bool adapt) {
     default: return nullptr;
     }
 }
+const void* batch_table_big_f32_gauss();
+const void* batch_table_big_f32_mix2();
+const void* batch_table_big_f32_flat();
+const void* batch_table_big_f32_genz_disc();
+const void* batch_table_big_f32_genz_ppeak();
+
+const void* batch_iterate_kernel_f32_big(int integrand) {
+    switch (integrand) {
+    case VEGAS_GAUSS: return batch_table_big_f32_gauss();
+    case VEGAS_GAUSS_MIX2: return batch_table_big_f32_mix2();
+    case VEGAS_FLAT: return batch_table_big_f32_flat();
+    case VEGAS_GENZ_DISC: return batch_table_big_f32_genz_disc();
+    case VEGAS_GENZ_PPEAK: return batch_table_big_f32_genz_ppeak();
+    default: return nullptr;
+    }
+}
 }  // namespace vegas

@@ -1,5 +1,6 @@
 // Instantiates the batch iterate kernel for float arithmetic and the VEGAS_FLAT
-// integrand.
+// integrand (and its big-block adapting variant).
 #include "batch_kernel.cuh"
 
 VEGAS_BATCH_TABLE(batch_table_f32_flat, float, VEGAS_FLAT)
+VEGAS_BATCH_TABLE_BIG(batch_table_big_f32_flat, VEGAS_FLAT)

@@ -97,8 +97,12 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchTile& 
     __syncthreads();  // the next tile restages the shared memory
 }
 
-template <typename R, int FN, bool ADAPT>
-__global__ void __launch_bounds__(256) batch_iterate_kernel(const BatchArgs a) {
+// BIG: the instantiation for one block of up to kBigBlockThreads per SM (float
+// adapting rounds whose 32 histogram copies for the widest integral miss the
+// default budget but fit that block), with its own launch bound.
+template <typename R, int FN, bool ADAPT, bool BIG = false>
+__global__ void __launch_bounds__(BIG ? kBigBlockThreads : 256)
+    batch_iterate_kernel(const BatchArgs a) {
     using P = Prec<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sred[32];
@@ -131,6 +135,8 @@ __global__ void __launch_bounds__(256) batch_iterate_kernel(const BatchArgs a) {
 // host (batch_f32.cu / batch_f64.cu; nullptr for an integrand it lacks)
 const void* batch_iterate_kernel_f32(int integrand, bool adapt);
 const void* batch_iterate_kernel_f64(int integrand, bool adapt);
+// the float big-block adapting kernel of an integrand (batch_f32.cu)
+const void* batch_iterate_kernel_f32_big(int integrand);
 
 }  // namespace vegas
 
@@ -141,5 +147,13 @@ const void* batch_iterate_kernel_f64(int integrand, bool adapt);
     const void* NAME(bool adapt) {                                              \
         return adapt ? (const void*)&batch_iterate_kernel<R, FN, true>          \
                      : (const void*)&batch_iterate_kernel<R, FN, false>;        \
+    }                                                                           \
+    }
+
+// The float big-block adapting kernel of one integrand, as NAME().
+#define VEGAS_BATCH_TABLE_BIG(NAME, FN)                                         \
+    namespace vegas {                                                           \
+    const void* NAME() {                                                        \
+        return (const void*)&batch_iterate_kernel<float, FN, true, true>;       \
     }                                                                           \
     }

@@ -274,3 +274,23 @@ def test_batch_init_refuses_bad_integrands_and_boxes():
         V.VegasBatch(dims, ns, 10, 1, V.VEGAS_FP64, [[], []], integrand=W.FLAT,
                      boxes=[None, [(0.0, 1.0), (1.0, 1.0), (0.0, 1.0)]])
     assert e.value.status == V.VEGAS_EINVAL
+
+
+def test_big_block_batch_round_equals_the_default_shape():
+    """Float adapting rounds whose 32 copies for the widest integral miss the
+    default budget run as one 768-thread block per SM; forcing the default
+    shape (128-thread blocks) gives the same samples, sums to float summation
+    order and the same refined grids to float rounding."""
+    dims, ns, params = small_batch()  # widest: d = 20 at N = 30, 600 bins
+    out = []
+    for bt in (256, 128):
+        B = V.VegasBatch(dims, ns, 30, 7, V.VEGAS_FP32_EVAL, params, max_iters=4)
+        B.config(block_threads=bt, tile_samples=8192)
+        B.run(1)
+        out.append((B.log()[:, 0], [B.grid(b) for b in range(len(dims))]))
+        B.close()
+    (lb, gb), (ld, gd) = out
+    assert np.array_equal(lb[:, 2:4], ld[:, 2:4])
+    assert np.allclose(lb[:, 4], ld[:, 4], rtol=1e-6, atol=0)
+    for b in range(len(dims)):
+        assert np.allclose(gb[b], gd[b], rtol=0, atol=1e-6), b
