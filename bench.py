@@ -486,30 +486,45 @@ def mix16_timing(V, stream):
     return res
 
 
+def timed_schedule(V, stream, dim, seed, mode, fid, params, reps=3):
+    """The d=8 workload's schedule (10 x 1e7 adapting, 5 x 1e8 fixed) on a
+    fresh state of this integrand: one untimed run first (it loads every kernel
+    the schedule uses), then `reps` timed runs on fresh states; the median ms
+    and the last run's combined result over the fixed-grid iterations."""
+    import torch
+
+    sched = [(N_ADAPT, 1)] * IT_ADAPT + [(N_FIXED, 0)] * IT_FIXED
+    ms, res = [], None
+    for r in range(reps + 1):
+        v = V.Vegas(dim, NBINS, seed, mode, fid, params, max_iters=IT_ADAPT + IT_FIXED,
+                    stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        v.run(sched, ALPHA)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r > 0:
+            ms.append(e0.elapsed_time(e1))
+        res = v.result(IT_ADAPT)
+        v.close()
+    return statistics.median(ms), res
+
+
 def gauss20_timing(V, stream):
     """The 20-dimensional symmetric Gaussian of Table 1 (Eq. 1, centres 1/2,
     a = 0.1 as in the d=8 workload, 50 bins) on the d=8 workload's schedule:
     10 adapting iterations of 1e7 samples, then 5 fixed-grid iterations of 1e8,
     in both precisions; the result combines the fixed-grid iterations and is
     compared with erf(5)^20."""
-    import torch
-
     from paper_2002_12921_b300 import workloads as W
 
     dim, a = 20, 0.1
     exact = math.erf(0.5 / a) ** dim
     res = {"exact": exact}
     for name, mode in (("fp32", V.VEGAS_FP32_EVAL), ("fp64", V.VEGAS_FP64)):
-        v = V.Vegas(dim, NBINS, 20, mode, V.VEGAS_GAUSS, W.gauss_params(dim, a),
-                    max_iters=IT_ADAPT + IT_FIXED, stream=stream)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        v.run([(N_ADAPT, 1)] * IT_ADAPT + [(N_FIXED, 0)] * IT_FIXED, ALPHA)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        m, sg, c2, n, bad = v.result(IT_ADAPT)
-        v.close()
+        ms, (m, sg, c2, n, bad) = timed_schedule(V, stream, dim, 20, mode, V.VEGAS_GAUSS,
+                                                 W.gauss_params(dim, a),
+                                                 reps=3 if name == "fp32" else 1)
         res[name] = {"ms": ms, "samples_per_s": SAMPLES_PER_STEP / (ms / 1e3), "mean": m,
                      "sigma": sg, "chi2_dof": c2, "pull": (m - exact) / sg}
     return res
@@ -520,8 +535,6 @@ def genz16_timing(V, stream):
     product peak, normalised to 1; seeded a_i, c_i), 50 bins, on the d=8
     workload's schedule (10 x 1e7 adapting, 5 x 1e8 fixed) in both precisions;
     the result combines the fixed-grid iterations and is compared with 1."""
-    import torch
-
     from paper_2002_12921_b300 import workloads as W
 
     res = {}
@@ -529,15 +542,8 @@ def genz16_timing(V, stream):
         p = W.genz_params(16, seed=16, kind=fid)
         res[fname] = {}
         for name, mode in (("fp32", V.VEGAS_FP32_EVAL), ("fp64", V.VEGAS_FP64)):
-            v = V.Vegas(16, NBINS, 16, mode, fid, p, max_iters=IT_ADAPT + IT_FIXED, stream=stream)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            v.run([(N_ADAPT, 1)] * IT_ADAPT + [(N_FIXED, 0)] * IT_FIXED, ALPHA)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
-            m, sg, c2, n, bad = v.result(IT_ADAPT)
-            v.close()
+            ms, (m, sg, c2, n, bad) = timed_schedule(V, stream, 16, 16, mode, fid, p,
+                                                     reps=3 if name == "fp32" else 1)
             res[fname][name] = {"ms": ms, "samples_per_s": SAMPLES_PER_STEP / (ms / 1e3),
                                 "mean": m, "sigma": sg, "chi2_dof": c2, "pull": (m - 1.0) / sg}
     return res
