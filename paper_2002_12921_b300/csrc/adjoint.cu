@@ -15,6 +15,7 @@
 #include <cfloat>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "iterate_kernel.cuh"
 
@@ -52,27 +53,82 @@ struct AdjointArgs {
     double scale[kMaxDim + 2];       // per component: 1, 2/(a c) (x d), 1/a
 };
 
-// Per component (I, d/dmu_k, d/da) a compensated sum of the values and their
-// squares; the count of non-finite weights.
+// Sums of one component's values and squares.  Double: plain sums.  Float:
+// plain float partial sums over a run of samples, each run's partials then
+// added into Kahan-compensated sums (fold); a partial of kFold values carries
+// a rounding of about kFold eps of its size, a few 1e-6 of the component's
+// Monte Carlo error, and the run costs 2 float operations per sample instead
+// of the compensated 8 -- with d + 2 components that is most of the float work.
+constexpr int kFold = 64;
+template <typename R>
+struct AdjAcc;
+template <>
+struct AdjAcc<double> {
+    double s1 = 0.0, s2 = 0.0;
+    __device__ __forceinline__ void add(double v) {
+        s1 += v;
+        s2 = fma(v, v, s2);
+    }
+    __device__ __forceinline__ void fold() {}
+    __device__ __forceinline__ double sum1() const { return s1; }
+    __device__ __forceinline__ double sum2() const { return s2; }
+};
+template <>
+struct AdjAcc<float> {
+    float p1 = 0.f, p2 = 0.f;                  // the current run's plain sums
+    float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;  // Kahan sums of the runs
+    __device__ __forceinline__ void add(float v) {
+        p1 += v;
+        p2 = fmaf(v, v, p2);
+    }
+    __device__ __forceinline__ void fold() {
+        const float y1 = p1 - c1;
+        const float t1 = s1 + y1;
+        c1 = (t1 - s1) - y1;
+        s1 = t1;
+        const float y2 = p2 - c2;
+        const float t2 = s2 + y2;
+        c2 = (t2 - s2) - y2;
+        s2 = t2;
+        p1 = p2 = 0.f;
+    }
+    __device__ __forceinline__ double sum1() const { return (double)s1 - (double)c1; }
+    __device__ __forceinline__ double sum2() const { return (double)s2 - (double)c2; }
+};
+
+// Per component (I, d/dmu_k, d/da) the sums of the values and their squares;
+// the count of non-finite weights.  The value-only pass keeps the iterate
+// kernels' per-sample compensated sums (with one component the runs cost more
+// than they save); finish() folds the last run.
 template <typename R, int D, bool GRAD>
 struct AdjointSink {
     static constexpr bool kNeedBins = false;
     static constexpr int NC = GRAD ? D + 2 : 1;
-    Acc<R> acc[NC];
+    static constexpr bool kRuns = GRAD && sizeof(R) == 4;
+    typename std::conditional<kRuns, AdjAcc<R>, Acc<R>>::type acc[NC];
     unsigned bad = 0;
+    int run = 0;
     R two_over_c2, dim;
     __device__ __forceinline__ AdjointSink(R t, R d) : two_over_c2(t), dim(d) {}
     template <typename F>
     __device__ __forceinline__ void operator()(R fw, const F& f, const uint32_t (&)[D]) {
         if (!Prec<R>::finite(fw)) {
             ++bad;
-            return;
-        }
-        acc[0].add(fw);
-        if (GRAD) {
+        } else {
+            acc[0].add(fw);
+            if (GRAD) {
 #pragma unroll
-            for (int k = 0; k < D; ++k) acc[1 + k].add(fw * f.z[k]);
-            acc[D + 1].add(fw * Prec<R>::fma(f.s, two_over_c2, -dim));
+                for (int k = 0; k < D; ++k) acc[1 + k].add(fw * f.z[k]);
+                acc[D + 1].add(fw * Prec<R>::fma(f.s, two_over_c2, -dim));
+            }
+        }
+        if (kRuns && ++run == kFold) finish();
+    }
+    __device__ __forceinline__ void finish() {
+        if constexpr (kRuns) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[c].fold();
+            run = 0;
         }
     }
 };
@@ -101,6 +157,7 @@ __global__ void __launch_bounds__(256) gauss_adjoint_kernel(const AdjointArgs a)
         (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x, a.n,
         (unsigned long long)gridDim.x * blockDim.x, a.iter, 0u, a.rk0, a.rk1, a.fc, N,
         (R)(sizeof(R) == 4 ? a.fc.C32 : a.fc.C), n4, nlast, sgrid, sink);
+    sink.finish();
 
     double* part = a.partials + (size_t)blockIdx.x * kStride;
 #pragma unroll
