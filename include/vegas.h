@@ -187,6 +187,12 @@ int vegas_refine(vegas_state *s, double alpha);
 int vegas_result(vegas_state *s, int first_iter, double *mean, double *sigma, double *chi2_dof,
                  int *n_iter);
 
+/* The same combination over iterations first_iter .. end_iter-1 only (for
+ * the running result after each iteration).  VEGAS_EINVAL if end_iter <=
+ * first_iter or iteration end_iter-1 is not logged.  Synchronises. */
+int vegas_result_range(vegas_state *s, int first_iter, int end_iter, double *mean,
+                       double *sigma, double *chi2_dof);
+
 /* Copy the log to host memory: row t = {S1, S2, n, nonfinite, I, var} for
  * t < min(max_rows, n_iter).  Synchronises the stream. */
 int vegas_get_iterations(vegas_state *s, double *host_rows, int max_rows, int *n_rows);

@@ -5,6 +5,7 @@ library ``_build/libvegas_b300.so``.  The functions keep the C names.  If the
 library is missing, the first call raises -- there is no CPU fallback.
 """
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -36,7 +37,7 @@ EXPORTED = ("vegas_workspace_bytes", "vegas_init_grid", "vegas_set_config", "veg
             "vegas_shard_import", "vegas_export_state", "vegas_import_state",
             "vegas_set_user_integrand", "vegas_get_iteration_times",
             "vegas_batch_set_tiles_by_dim", "vegas_set_box", "vegas_pipe_peak",
-            "vegas_inject_failure", "vegas_batch_init_integrand")
+            "vegas_inject_failure", "vegas_batch_init_integrand", "vegas_result_range")
 
 
 class VegasError(RuntimeError):
@@ -71,6 +72,7 @@ def lib():
         L.vegas_set_config.argtypes = [vp, ctypes.POINTER(vegas_config)]
         L.vegas_set_box.argtypes = [vp, vp, vp]
         L.vegas_inject_failure.argtypes = [vp, i32]
+        L.vegas_result_range.argtypes = [vp, i32, i32, vp, vp, vp]
         L.vegas_pipe_peak.argtypes = [ctypes.c_int, ctypes.c_uint32, vp, ctypes.c_size_t, vp,
                                       vp]
         L.vegas_iterate.argtypes = [vp, u64, i32]
@@ -201,6 +203,16 @@ def vegas_result(h, first_iter=0):
     if rc not in (VEGAS_OK, VEGAS_ENONFINITE):
         raise VegasError(rc, "vegas_result")
     return m.value, s.value, c.value, n.value, rc == VEGAS_ENONFINITE
+
+
+def vegas_result_range(h, first_iter, end_iter):
+    """(mean, sigma, chi2_dof, nonfinite_seen) over iterations [first, end)."""
+    m, s, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = lib().vegas_result_range(h, first_iter, end_iter, ctypes.byref(m), ctypes.byref(s),
+                                  ctypes.byref(c))
+    if rc not in (VEGAS_OK, VEGAS_ENONFINITE):
+        raise VegasError(rc, "vegas_result_range")
+    return m.value, s.value, c.value, rc == VEGAS_ENONFINITE
 
 
 def vegas_get_iterations(h, max_rows=1 << 16):
@@ -385,6 +397,22 @@ class Vegas:
 
     def iterations(self):
         return vegas_get_iterations(self.handle, self.max_iters)
+
+    def records(self, first_iter=0):
+        """One record per logged iteration t >= first_iter: its samples, I,
+        sigma (= sqrt(var)), non-finite count, device time (ms) and rate, and
+        the combined result over iterations first_iter .. t (the running
+        estimate, its sigma and chi^2 per degree of freedom)."""
+        rows, ns = self.iterations(), self.iteration_times()
+        out = []
+        for t in range(first_iter, len(rows)):
+            mean, sigma, chi2, _ = vegas_result_range(self.handle, first_iter, t + 1)
+            ms = ns[t] / 1e6
+            out.append({"iter": t, "n": int(rows[t][2]), "I": rows[t][4],
+                        "sigma": math.sqrt(rows[t][5]), "nonfinite": int(rows[t][3]),
+                        "device_ms": ms, "samples_per_s": rows[t][2] / (ms / 1e3) if ms > 0 else None,
+                        "mean_so_far": mean, "sigma_so_far": sigma, "chi2_dof_so_far": chi2})
+        return out
 
     def iteration_times(self):
         """Device time of each logged iteration, ns."""

@@ -641,6 +641,29 @@ int vegas_result(vegas_state* s, int first_iter, double* mean, double* sigma, do
     return bad ? VEGAS_ENONFINITE : VEGAS_OK;
 }
 
+int vegas_result_range(vegas_state* s, int first_iter, int end_iter, double* mean,
+                       double* sigma, double* chi2_dof) {
+    if (!s || first_iter < 0 || end_iter <= first_iter) return VEGAS_EINVAL;
+    DeviceGuard g(s->device);
+    if (!g.ok) return VEGAS_ECUDA;
+    double* rows = new (std::nothrow) double[(size_t)s->max_iters * kLogStride];
+    if (!rows) return VEGAS_EINVAL;
+    int n = 0, bad = 0;
+    int rc = read_log(s, rows, s->max_iters, &n, nullptr, first_iter);
+    if (rc == VEGAS_OK && end_iter > n) rc = VEGAS_EINVAL;  // not logged (yet)
+    if (rc == VEGAS_OK) {
+        for (int t = first_iter; t < end_iter; ++t)
+            if (rows[(size_t)t * kLogStride + 3] != 0.0) bad = 1;
+        double m = NAN, sg = NAN, c2 = NAN;
+        combine_rows(rows, kLogStride, first_iter, end_iter, &m, &sg, &c2);
+        if (mean) *mean = m;
+        if (sigma) *sigma = sg;
+        if (chi2_dof) *chi2_dof = c2;
+    }
+    delete[] rows;
+    return rc != VEGAS_OK ? rc : (bad ? VEGAS_ENONFINITE : VEGAS_OK);
+}
+
 int vegas_get_iterations(vegas_state* s, double* host_rows, int max_rows, int* n_rows) {
     if (!s || !host_rows || max_rows < 0 || !n_rows) return VEGAS_EINVAL;
     DeviceGuard g(s->device);

@@ -313,6 +313,32 @@ def test_big_block_adapting_shape_equals_the_default_shape(fid, dim, nbins):
     assert np.allclose(hb, hd, rtol=1e-5, atol=1e-30 * np.max(hd))
 
 
+def test_running_records_combine_like_the_oracle():
+    """Vegas.records(): per iteration its own estimate and the combination of
+    iterations first .. t (vegas_result_range), which equals the oracle's
+    combination of the same logged rows and, at the last row, vegas_result."""
+    p = W.gauss_params(5, 0.15)
+    v = V.Vegas(5, 40, 8, V.VEGAS_FP64, W.GAUSS, p, max_iters=8)
+    v.run([(100_000, 1)] * 4 + [(200_000, 0)] * 3)
+    rows, recs = v.iterations(), v.records(first_iter=2)
+    assert [r["iter"] for r in recs] == list(range(2, 7))
+    for r in recs:
+        t = r["iter"]
+        assert r["I"] == rows[t][4] and r["n"] == rows[t][2]
+        assert r["device_ms"] > 0 and r["samples_per_s"] > 0
+        om, osg, oc = oracle.combine(rows[2:t + 1, 4], rows[2:t + 1, 5])
+        assert abs(r["mean_so_far"] - om) <= 1e-13 * abs(om)
+        assert abs(r["sigma_so_far"] - osg) <= 1e-13 * osg
+        assert abs(r["chi2_dof_so_far"] - oc) <= 1e-12 * max(oc, 1.0)
+    assert recs[0]["chi2_dof_so_far"] == 0.0
+    assert abs(recs[0]["sigma_so_far"] - recs[0]["sigma"]) <= 1e-15 * recs[0]["sigma"]
+    assert recs[-1]["mean_so_far"] == v.result(2)[0]
+    with pytest.raises(V.VegasError) as e:  # not logged
+        V.binding.vegas_result_range(v.handle, 0, 8)
+    assert e.value.status == V.VEGAS_EINVAL
+    v.close()
+
+
 def test_tuning_table_with_the_real_autotuner(tmp_path):
     """TuningTable over the GPU autotuner: the stored choice is one of the
     candidates, is reused from the file, and keeps results."""
