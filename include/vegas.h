@@ -118,7 +118,11 @@ extern "C" {
 
 typedef struct vegas_state vegas_state; /* opaque host descriptor */
 
-/* Launch configuration; zeros select the defaults. */
+/* Launch configuration; zeros select the defaults.  Under the defaults, a
+ * float adapting iteration whose 32 per-lane histogram copies exceed the
+ * default shared-memory budget (dim * nbins > 416) but fit one block runs as
+ * one 768-thread block per SM instead (the same occupancy, no shared copies);
+ * setting block_threads or blocks_per_sm keeps the configured shape. */
 typedef struct {
     int block_threads;    /* threads per block of the iterate kernel (multiple of 32,
                              32 .. 256); default 256 */
@@ -308,7 +312,9 @@ int vegas_batch_init_integrand(vegas_batch **out, int count, const int *dims,
                                const double *box_hi, int max_iters, void *d_workspace,
                                size_t ws_bytes, void *cuda_stream);
 /* Block size (32..256, multiple of 32) and samples per tile (>= 4096, multiple
- * of 32); 0 keeps the current value.  Rebuilds the tile table. */
+ * of 32); 0 keeps the current value.  Rebuilds the tile table.  At the default
+ * block size (256), float adapting rounds run as one 768-thread block per SM
+ * when 32 histogram copies for the widest integral need it and fit. */
 int vegas_batch_set_config(vegas_batch *b, int block_threads, uint64_t tile_samples);
 /* Samples per tile by dimension: tiles[d-1] for the integrals of dimension d
  * (d = 1 .. count, count <= VEGAS_MAX_DIM; each 0 = the vegas_batch_set_config
