@@ -477,9 +477,43 @@ struct IterateSink {
             acc.add(fw);
             if (ADAPT) {
                 const R fw2 = fw * fw;
+                if constexpr (sizeof(H) == 4) {
+                    // The float shared-memory atomic add is a compare-and-swap
+                    // loop on this GPU, and D of them in a row are D dependent
+                    // round trips.  Groups of 4 dimensions instead: 4 loads, then
+                    // 4 compare-and-swaps issued back to back, then a plain
+                    // atomic add for any that lost a race with another warp
+                    // (lanes own their copies, so within a warp none can).  One
+                    // round trip per group: d=16 adapting iterations 6-9%
+                    // faster, d=8 1%; a won swap stores old + v rounded to
+                    // nearest, as the atomic add does.
+                    unsigned* su = reinterpret_cast<unsigned*>(shist);
 #pragma unroll
-                for (int k = 0; k < D; ++k)
-                    atomicAdd(&shist[((k * N + (int)bins[k]) << logr) | lane_copy], (H)fw2);
+                    for (int k0 = 0; k0 < D; k0 += 4) {
+                        constexpr int G = 4;
+                        float old[G];
+#pragma unroll
+                        for (int g = 0; g < G; ++g)
+                            if (k0 + g < D)
+                                old[g] = shist[(((k0 + g) * N + (int)bins[k0 + g]) << logr) | lane_copy];
+                        unsigned got[G];
+#pragma unroll
+                        for (int g = 0; g < G; ++g)
+                            if (k0 + g < D)
+                                got[g] = atomicCAS(
+                                    &su[(((k0 + g) * N + (int)bins[k0 + g]) << logr) | lane_copy],
+                                    __float_as_uint(old[g]), __float_as_uint(old[g] + (float)fw2));
+#pragma unroll
+                        for (int g = 0; g < G; ++g)
+                            if (k0 + g < D && got[g] != __float_as_uint(old[g]))
+                                atomicAdd(&shist[(((k0 + g) * N + (int)bins[k0 + g]) << logr) | lane_copy],
+                                          (H)fw2);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < D; ++k)
+                        atomicAdd(&shist[((k * N + (int)bins[k]) << logr) | lane_copy], (H)fw2);
+                }
             }
         } else {
             ++bad;
