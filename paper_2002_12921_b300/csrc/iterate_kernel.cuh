@@ -461,6 +461,22 @@ __device__ __forceinline__ void report_checks(bool ok, unsigned* ctrl) {
 
 // The iterate kernels' sink: per-thread sums of f J and (f J)^2, the count of
 // non-finite weights, and (ADAPT) the shared histogram.
+// The bit pattern of a histogram value, for compare-and-swap.
+template <typename H>
+struct HistBits;
+template <>
+struct HistBits<float> {
+    using type = unsigned;
+    static __device__ __forceinline__ unsigned bits(float v) { return __float_as_uint(v); }
+};
+template <>
+struct HistBits<double> {
+    using type = unsigned long long;
+    static __device__ __forceinline__ unsigned long long bits(double v) {
+        return (unsigned long long)__double_as_longlong(v);
+    }
+};
+
 template <typename R, int D, bool ADAPT>
 struct IterateSink {
     static constexpr bool kNeedBins = ADAPT;
@@ -486,26 +502,29 @@ struct IterateSink {
                     // (lanes own their copies, so within a warp none can).  One
                     // round trip per group: d=16 adapting iterations 6-9%
                     // faster, d=8 1%; a won swap stores old + v rounded to
-                    // nearest, as the atomic add does.
-                    unsigned* su = reinterpret_cast<unsigned*>(shist);
+                    // nearest, as the atomic add does.  (The double histograms
+                    // keep the plain atomic add: the FP64 kernels are bound by
+                    // the FP64 pipe, and grouping measured no faster there.)
+                    using B = typename HistBits<H>::type;
+                    B* su = reinterpret_cast<B*>(shist);
 #pragma unroll
                     for (int k0 = 0; k0 < D; k0 += 4) {
                         constexpr int G = 4;
-                        float old[G];
+                        H old[G];
 #pragma unroll
                         for (int g = 0; g < G; ++g)
                             if (k0 + g < D)
                                 old[g] = shist[(((k0 + g) * N + (int)bins[k0 + g]) << logr) | lane_copy];
-                        unsigned got[G];
+                        B got[G];
 #pragma unroll
                         for (int g = 0; g < G; ++g)
                             if (k0 + g < D)
                                 got[g] = atomicCAS(
                                     &su[(((k0 + g) * N + (int)bins[k0 + g]) << logr) | lane_copy],
-                                    __float_as_uint(old[g]), __float_as_uint(old[g] + (float)fw2));
+                                    HistBits<H>::bits(old[g]), HistBits<H>::bits(old[g] + (H)fw2));
 #pragma unroll
                         for (int g = 0; g < G; ++g)
-                            if (k0 + g < D && got[g] != __float_as_uint(old[g]))
+                            if (k0 + g < D && got[g] != HistBits<H>::bits(old[g]))
                                 atomicAdd(&shist[(((k0 + g) * N + (int)bins[k0 + g]) << logr) | lane_copy],
                                           (H)fw2);
                     }
