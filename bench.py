@@ -107,11 +107,25 @@ def add_product_fractions(peak, adjoint, batch, mix16, gauss20, genz16):
 
 
 def alg_ops_per_sample(d):
-    """Algorithmic lane-operations of one FP32 fixed-grid sample: Philox (10
-    rounds x 2 wide multiplies + 2 three-input xors per call), per dimension
-    bin/position multiplies, fraction (2), grid load, map fma, Jacobian multiply
-    and two integrand fmas (9), one N^4 multiply per call, and 13 per sample
-    (exponential 2, weight 1, Kahan 8 + square 1, finiteness 1)."""
+    """Issue slots of one FP32 fixed-grid sample as the method's steps count
+    them (the roofline's `achieved`): Philox4x32-10 at 60 per call (10 rounds
+    x (2 wide multiplies + 2 xors + 2 round-key additions)); per dimension 7
+    (the bin split's wide multiply, the integer-to-float conversion, the map's
+    fma, the Jacobian multiply, the shared-memory load of the bin, and the
+    Gaussian's subtraction and fma); per sample 12 (the exponential, 3
+    multiplies for the weight, 8 for the compensated sums of f J and its
+    square).  188 at d = 8."""
+    return 60 * ((d + 3) // 4) + 7 * d + 12
+
+
+def kernel_ops_per_sample(d):
+    """The leaner count of the same sample as the kernel issues it: the round
+    keys k + r W depend only on the seed, so they are computed once per launch
+    rather than per call (40 per call: 10 rounds x (2 wide multiplies + 2
+    three-input xors)); per dimension the bin/position multiplies, the
+    fraction (2), the grid load, the map fma, the Jacobian multiply and two
+    integrand fmas (9); one N^4 multiply per call; and 13 per sample
+    (exponential 2, weight 1, Kahan 8 + square 1, finiteness 1).  167 at d = 8."""
     calls = (d + 3) // 4
     return 40 * calls + 9 * d + calls + 13
 
@@ -146,14 +160,15 @@ class Clocks:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index):
+    def __init__(self, gpu_id):
         import threading
 
         self.rows = []
+        self.gpu_id = gpu_id
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "50", "-i", str(device_index)], stdout=subprocess.PIPE,
+                 "-lms", "50", "-i", str(gpu_id)], stdout=subprocess.PIPE,
                 stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -175,7 +190,8 @@ class Clocks:
 
     def stop(self, window=None):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "gpu": self.gpu_id}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -190,7 +206,7 @@ class Clocks:
         rows = [r for _, r in rows]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples in window"],
-                    "samples": 0}
+                    "samples": 0, "gpu": self.gpu_id}
 
         def num(x):
             try:
@@ -209,8 +225,21 @@ class Clocks:
         loaded = [s for s in sm if s >= 0.5 * max(sm)] if sm else []
         return {"sm_mhz": statistics.median(loaded) if loaded else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(rows),
+                "samples": len(rows), "gpu": self.gpu_id,
                 "power_w_max": max((num(r[2]) or 0.0) for r in rows)}
+
+
+def smi_gpu_id(device):
+    """nvidia-smi's name for CUDA device `device`: its UUID.  nvidia-smi numbers
+    GPUs in PCI order and ignores CUDA_VISIBLE_DEVICES, so the CUDA index can
+    name another job's GPU on a shared machine; the UUID cannot."""
+    import torch
+
+    try:
+        u = str(torch.cuda.get_device_properties(device).uuid)
+    except (AttributeError, RuntimeError):
+        return str(device)
+    return u if u.startswith(("GPU-", "MIG-")) else "GPU-" + u
 
 
 def clocks_rejected(clk):
@@ -263,7 +292,8 @@ def run_step_sharded(V, stream, mode, seed, world, fixed_events=None):
 
     v = V.Vegas(DIM, NBINS, seed, mode, V.VEGAS_GAUSS, W.gauss_params(DIM, A),
                 max_iters=IT_ADAPT + IT_FIXED, stream=stream)
-    sv = ShardedVegas(GpuShardEngine(v))
+    # the ranks' grids are compared once per step (after the last refinement)
+    sv = ShardedVegas(GpuShardEngine(v), check_every=IT_ADAPT)
     for _ in range(IT_ADAPT):
         sv.iterate(N_ADAPT * world, True, ALPHA)
     for _ in range(IT_FIXED):
@@ -458,10 +488,15 @@ def mix16_timing(V, stream):
     a = wl.params[0]
     J = lambda c: 0.5 * (math.erf((1 - c) / a) + math.erf(c / a))  # noqa: E731
     exact = 0.5 * (J(1 / 3) ** 16 + J(2 / 3) ** 16)
-    res = {"exact": exact,
+    # one peak's share, J(1/3)^16 / 2 (= J(2/3)^16 / 2): the value a grid locked
+    # onto one peak converges to
+    locked = 0.5 * J(1 / 3) ** 16
+    res = {"exact": exact, "locked_peak_value": locked,
            "note": "a separable grid cannot hold both diagonal peaks; it locks onto one, as "
-                   "the FP64 oracle's does, and the estimate tends to half the integral: "
-                   "the pull measures that, not an arithmetic error"}
+                   "the FP64 oracle's does (tests/test_oracle_iterate.py), and the estimate "
+                   "tends to half the integral: pull measures that against the full "
+                   "integral, pull_locked against the locked peak's value"}
+    rows = {}
     for name, mode, iters in (("fp32", V.VEGAS_FP32_EVAL, 20), ("fp64", V.VEGAS_FP64, 2)):
         v = V.Vegas(16, 100, wl.seed, mode, V.VEGAS_GAUSS_MIX2, wl.params, max_iters=32,
                     stream=stream)
@@ -474,6 +509,7 @@ def mix16_timing(V, stream):
         ms = e0.elapsed_time(e1)
         m, sg, c2, n, bad = v.result(iters // 2)
         e = v.grid()
+        rows[name] = v.iterations()
         v.close()
         # bins whose centre lies within 0.1 of each peak, averaged over dimensions
         mids = (e[:, :-1] + e[:, 1:]) / 2
@@ -482,7 +518,16 @@ def mix16_timing(V, stream):
         res[name] = {"iterations": iters, "ms": ms,
                      "samples_per_s": iters * wl.schedule[0][0] / (ms / 1e3),
                      "mean": m, "sigma": sg, "chi2_dof": c2, "pull": (m - exact) / sg,
+                     "pull_locked": (m - locked) / sg,
                      "bins_near_1/3": near_a, "bins_near_2/3": near_b}
+    # the two precisions on the same iterations (same counters): iteration 0
+    # on the same uniform grid, iteration 1 on each one's own first refinement
+    res["fp32_vs_fp64_same_iterations"] = [
+        {"iteration": t, "I_fp32": float(rows["fp32"][t][4]), "I_fp64": float(rows["fp64"][t][4]),
+         "abs_diff_in_sigma": abs(rows["fp32"][t][4] - rows["fp64"][t][4])
+         / math.sqrt(rows["fp64"][t][5]),
+         "sigma_ratio_fp32_fp64": math.sqrt(rows["fp32"][t][5] / rows["fp64"][t][5])}
+        for t in range(2)]
     return res
 
 
@@ -613,13 +658,16 @@ def cpu_baseline(fast=False):
         n1 = sum(s for s, _ in sched1)
         out["single_core"] = {"value": n1 / dt1, "unit": "samples/s",
                               "sample": f"{n1:.1e} samples (1e6 adapting + 2e6 fixed), 1 thread"}
-        # the d=16 two-peak mixture: one adapting iteration of 2e6 samples
+        # the d=16 two-peak mixture: one 1e8-sample launch chunk of its first
+        # (adapting, uniform-grid) iteration, as the GPU streams it
         wl = W.c5_mix16()
         t0 = time.perf_counter()
-        oracle.run(16, 100, wl.seed, W.GAUSS_MIX2, wl.params, [(2_000_000, 1)], nthreads=cores)
-        out["mix16"] = {"value": 2_000_000 / (time.perf_counter() - t0), "unit": "samples/s",
-                        "sample": "d=16 mixture, one adapting iteration of 2e6 samples, "
-                                  f"{cores} threads"}
+        oracle.iterate_range(oracle.uniform_grid(16, 100), wl.seed, 0, 0, wl.chunk,
+                             W.GAUSS_MIX2, wl.params, True, nthreads=cores)
+        dt16 = time.perf_counter() - t0
+        out["mix16"] = {"value": wl.chunk / dt16, "unit": "samples/s", "seconds": dt16,
+                        "sample": f"d=16 mixture, one {wl.chunk:.0e}-sample chunk of an "
+                                  f"adapting iteration (the GPU's launch size), {cores} threads"}
     return out
 
 
@@ -694,7 +742,7 @@ def main():
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        clocks = Clocks(torch.cuda.current_device())
+        clocks = Clocks(smi_gpu_id(torch.cuda.current_device()))
         clocks.wait_ready()
         ms32, fixed32, res32 = time_mode(V, V.VEGAS_FP32_EVAL, args.steps, max(3, args.warmup),
                                          seed_main, ws, flush, stream, world)
@@ -748,11 +796,18 @@ def main():
     fixed_ms = statistics.mean(fixed32)
     ops = alg_ops_per_sample(DIM) * N_FIXED
     achieved = ops / (fixed_ms / 1e3) / 1e12
+    kernel_achieved = kernel_ops_per_sample(DIM) * N_FIXED / (fixed_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS,
                 "unit": "Tops/s", "frac": achieved / ALU_PEAK_TOPS,
+                "frac_issue": achieved / ALU_PEAK_TOPS,
+                "frac_issue_kernel_count": kernel_achieved / ALU_PEAK_TOPS,
                 "traffic": ITERATE_TRAFFIC_BYTES,
                 "kernel": "vegas_iterate_kernel<float,8,GAUSS,fixed>",
                 "kernel_ms": fixed_ms, "ops_per_sample": alg_ops_per_sample(DIM),
+                "ops_per_sample_kernel_count": kernel_ops_per_sample(DIM),
+                "ops_basis": "the method's steps per sample, Philox round-key additions "
+                             "included (frac, frac_issue); the kernel computes the round keys "
+                             "once per launch (frac_issue_kernel_count)",
                 "peak_basis": "148 SMs x 128 lanes x 2032 MHz (recipe unit counts and max clock)",
                 # the unit that binds inside that envelope (ncu full capture of this
                 # kernel build: fraction of elapsed cycles the pipe was busy)
@@ -806,8 +861,9 @@ def main():
                                        "per iteration" if world > 1 else "1 GPU")},
             "clocks": clk,
             "e2e": e2e,
-            # sharded: one more kernel per iteration installs the reduced sums
-            "gpu_launches": (LAUNCHES_PER_STEP + (IT_ADAPT + IT_FIXED if world > 1 else 0))
+            # sharded: one more kernel per iteration installs the reduced sums,
+            # and one per step digests the grid for the ranks' comparison
+            "gpu_launches": (LAUNCHES_PER_STEP + (IT_ADAPT + IT_FIXED + 1 if world > 1 else 0))
             * args.steps,
             "roofline": roofline,
             "cpu_baseline": cpu,

@@ -147,8 +147,10 @@ int vegas_workspace_bytes(int dim, int nbins, int max_iters, size_t *bytes);
  *   d_workspace, ws_bytes  device buffer owned by the caller; it must outlive
  *              the state and must not be used by anything else meanwhile
  *   cuda_stream  the stream all work of this state is ordered on
- * On success *out receives the descriptor.  Asynchronous: the workspace is
- * initialised by work enqueued on the stream. */
+ * On success *out receives the descriptor, which owns a small pinned host
+ * buffer (cudaHostAlloc: the control words and up to 4096 log rows) through
+ * which every later read of the log goes; VEGAS_ECUDA if it cannot be had.
+ * Asynchronous: the workspace is initialised by work enqueued on the stream. */
 int vegas_init_grid(vegas_state **out, int dim, int nbins, uint64_t seed, int mode, int integrand,
                     const double *params, int nparams, int max_iters, void *d_workspace,
                     size_t ws_bytes, void *cuda_stream);
@@ -185,14 +187,18 @@ int vegas_refine(vegas_state *s, double alpha);
 
 /* Combine iterations first_iter .. n_iter-1 (inverse-variance weighted mean,
  * sigma = (sum 1/var)^-1/2, chi^2 per degree of freedom; an iteration with
- * zero variance makes it the plain mean with sigma 0).  Synchronises the
+ * zero variance makes it the plain mean with sigma 0): the cumulative
+ * estimate of Lepage 1978 Sec. 2, which VegasFlow reports as its value +-
+ * error (Table 1).  The log is read through the descriptor's pinned host
+ * staging.  Synchronises the
  * stream.  Any output pointer may be NULL.  Returns VEGAS_ENONFINITE (after
  * filling the outputs) if a combined iteration saw non-finite f*J. */
 int vegas_result(vegas_state *s, int first_iter, double *mean, double *sigma, double *chi2_dof,
                  int *n_iter);
 
-/* The same combination over iterations first_iter .. end_iter-1 only (for
- * the running result after each iteration).  VEGAS_EINVAL if end_iter <=
+/* The same combination (Lepage 1978 Sec. 2's cumulative estimate) over
+ * iterations first_iter .. end_iter-1 only (for the running result after each
+ * iteration, as an integrator prints it per iteration).  VEGAS_EINVAL if end_iter <=
  * first_iter or iteration end_iter-1 is not logged.  Synchronises. */
 int vegas_result_range(vegas_state *s, int first_iter, int end_iter, double *mean,
                        double *sigma, double *chi2_dof);
@@ -208,7 +214,9 @@ int vegas_get_iterations(vegas_state *s, double *host_rows, int max_rows, int *n
  * host_ns: max_rows doubles; *n_rows receives the count.  Synchronises. */
 int vegas_get_iteration_times(vegas_state *s, double *host_ns, int max_rows, int *n_rows);
 
-/* Copy the grid (dim x (nbins+1) doubles, row-major) to / from host memory.
+/* Copy the grid -- the adaptive map's bin edges e_{k,0..N} per dimension
+ * (Lepage 1978 Sec. 3), which the after-iteration step of VegasFlow Sec. 2.2
+ * refines -- (dim x (nbins+1) doubles, row-major) to / from host memory.
  * vegas_set_grid checks e_0 = 0, e_N = 1 and strict increase (VEGAS_ESTATE
  * otherwise).  Both synchronise the stream. */
 int vegas_get_grid(vegas_state *s, double *host_edges);
@@ -340,6 +348,12 @@ int vegas_batch_result(vegas_batch *b, int index, int first_iter, double *mean, 
 int vegas_batch_get_log(vegas_batch *b, double *host_rows);
 /* Grid of integral `index`: dims[index] x (nbins+1) doubles.  Synchronises. */
 int vegas_batch_get_grid(vegas_batch *b, int index, double *host_edges);
+/* The (fJ)^2 histogram (Lepage 1978 Sec. 3's per-bin accumulator) that the
+ * last adapting iteration of integral `index` refined its grid from:
+ * dims[index] x nbins doubles (zeros before the first adapting iteration).
+ * The batch keeps a copy of every row as it refines it (VegasFlow Sec. 2.3:
+ * exporting histograms during integration).  Synchronises. */
+int vegas_batch_get_histogram(vegas_batch *b, int index, double *host_hist);
 int vegas_batch_destroy(vegas_batch *b);
 
 /* ---- entry point for callers that cannot allocate device memory ---------- */
@@ -362,9 +376,12 @@ int vegas_batch_destroy(vegas_batch *b);
  *   - dim * nbins > VEGAS_NOALLOC_MAX_DIM_X_BINS returns VEGAS_ENOSPACE (the
  *     histogram would not fit the scratch); the launch never uses more than
  *     VEGAS_NOALLOC_MAX_BLOCKS blocks.
- *   - The first call on a device looks up the scratch's device address on that
- *     device (cudaGetSymbolAddress); make that first call before any stream
- *     capture starts.
+ *   - d_edges and d_result must be device memory of one device (else
+ *     VEGAS_EINVAL, before anything is enqueued).
+ *   - A call looks up the scratch's device address on that device
+ *     (cudaGetSymbolAddress), afresh whenever its stream is not capturing, so
+ *     a context torn down and rebuilt in between (cudaDeviceReset) is seen;
+ *     make the first call on each device before any stream capture starts.
  *   - Every call shares the one scratch array and it keeps the last call's
  *     contents; each call clears what must start at zero.  Calls whose work
  *     overlaps on the GPU (other streams, other host threads) race on the
@@ -379,8 +396,24 @@ int vegas_iterate_noalloc(double *d_edges, int dim, int nbins, uint64_t seed, ui
                           int mode, const double *params, int nparams, uint64_t n_samples,
                           int adapt, double alpha, double *d_result, void *cuda_stream);
 
+/* A 64-bit digest of the grid's bit patterns, for checking that the ranks
+ * of a sharded integral hold identical grids after a refinement (the exchange
+ * above keeps them equal only if every rank receives the same totals):
+ *   digest = sum over the dim*(nbins+1) edges i (row-major) of
+ *            bits(e_i) * (splitmix64(i) | 1)   mod 2^64,
+ * splitmix64 being Vigna's SplitMix64 output function applied to i.  Equal
+ * grids give equal digests; grids that differ in one edge's bits never do.
+ * Writes {digest, ~digest} to d_out (2 uint64 of caller device memory, 8-byte
+ * aligned): one all-reduce of the pair with MAX then yields the largest digest
+ * and the complement of the smallest.  Asynchronous on the stream. */
+int vegas_grid_digest(vegas_state *s, uint64_t *d_out);
+
 /* ---- checkpoint / resume -------------------------------------------------- */
-/* A state's resumable content as a flat little-endian blob: shape, mode,
+/* A state's resumable content as a flat little-endian blob -- what the
+ * per-event and after-iteration steps of VegasFlow Sec. 2.2 carry from one
+ * iteration to the next (the grid, the accumulated histogram, the
+ * per-iteration estimates of Lepage 1978 Sec. 2-3); the paper itself
+ * describes no checkpointing.  Contents: shape, mode,
  * integrand and its parameters, seed, iteration count, launch configuration,
  * the grid, the histogram (an adapting iteration not yet refined), the
  * iteration log and the box (vegas_set_box; format version 2, version-1 blobs
@@ -465,8 +498,8 @@ int vegas_pipe_peak(int op, uint32_t iters, void *d_scratch, size_t scratch_byte
  * countdown 0 cancels.  Host-side only.  VEGAS_EINVAL for countdown < 0. */
 int vegas_inject_failure(vegas_state *s, int countdown);
 
-/* Release the descriptor (not the caller's workspace).  Synchronises the
- * stream first.  NULL is accepted. */
+/* Release the descriptor and its pinned host staging (not the caller's
+ * workspace).  Synchronises the stream first.  NULL is accepted. */
 int vegas_destroy(vegas_state *s);
 
 /* Static text for a status code. */

@@ -33,11 +33,13 @@ EXPORTED = ("vegas_workspace_bytes", "vegas_init_grid", "vegas_set_config", "veg
             "vegas_batch_workspace_bytes", "vegas_batch_init", "vegas_batch_set_config",
             "vegas_batch_set_stream", "vegas_batch_reset", "vegas_batch_iterate",
             "vegas_batch_result", "vegas_batch_get_log", "vegas_batch_get_grid",
+            "vegas_batch_get_histogram",
             "vegas_batch_destroy", "vegas_iterate_range", "vegas_shard_export",
             "vegas_shard_import", "vegas_export_state", "vegas_import_state",
             "vegas_set_user_integrand", "vegas_get_iteration_times",
             "vegas_batch_set_tiles_by_dim", "vegas_set_box", "vegas_pipe_peak",
-            "vegas_inject_failure", "vegas_batch_init_integrand", "vegas_result_range")
+            "vegas_inject_failure", "vegas_batch_init_integrand", "vegas_result_range",
+            "vegas_grid_digest")
 
 
 class VegasError(RuntimeError):
@@ -101,10 +103,12 @@ def lib():
         L.vegas_batch_result.argtypes = [vp, i32, i32, dp, dp, dp, ip]
         L.vegas_batch_get_log.argtypes = [vp, vp]
         L.vegas_batch_get_grid.argtypes = [vp, i32, vp]
+        L.vegas_batch_get_histogram.argtypes = [vp, i32, vp]
         L.vegas_batch_destroy.argtypes = [vp]
         L.vegas_iterate_range.argtypes = [vp, u64, u64, u64, i32]
         L.vegas_shard_export.argtypes = [vp, vp]
         L.vegas_shard_import.argtypes = [vp, vp, u64]
+        L.vegas_grid_digest.argtypes = [vp, vp]
         L.vegas_export_state.argtypes = [vp, vp, ctypes.POINTER(sz)]
         L.vegas_import_state.argtypes = [ctypes.POINTER(vp), vp, sz, vp, sz, vp]
         L.vegas_set_user_integrand.argtypes = [vp, vp, vp]
@@ -648,6 +652,13 @@ class VegasBatch:
         _check(lib().vegas_batch_get_grid(self.handle, index, e.ctypes.data),
                "vegas_batch_get_grid")
         return e
+
+    def histogram(self, index):
+        """The (f J)^2 histogram integral `index`'s last refinement used."""
+        h = np.empty((self.dims[index], self.nbins))
+        _check(lib().vegas_batch_get_histogram(self.handle, index, h.ctypes.data),
+               "vegas_batch_get_histogram")
+        return h
 
     def close(self):
         if self.handle:

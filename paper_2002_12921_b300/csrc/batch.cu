@@ -32,6 +32,7 @@ struct PostArgs {
     float2* staged32;  // float path: staged pairs of every row (hist layout), else null
     double* edges;
     double* hist;
+    double* hist_last;  // every row's histogram as the last refinement used it
     double* acc;
     double* log;
     unsigned* ctrl;
@@ -42,7 +43,8 @@ struct PostArgs {
 };
 
 // Block r: dimension rows[r].k of integral rows[r].b.  Adapting iterations
-// refine the row (and clear its histogram); the block of dimension 0 records
+// keep a copy of the row's histogram (vegas_batch_get_histogram), then refine
+// the row (and clear its histogram); the block of dimension 0 records
 // the integral's estimate I = S1/n, var = (S2/n - I^2)/(n-1) in its log row
 // `iter` and clears the accumulators; block 0 resets the tile ticket.
 __global__ void __launch_bounds__(kPostThreads) batch_post_kernel(const PostArgs a) {
@@ -53,7 +55,10 @@ __global__ void __launch_bounds__(kPostThreads) batch_post_kernel(const PostArgs
     const int N = a.nbins;
     if (a.adapt) {
         double* e = a.edges + info.edge_off + (size_t)row.k * (N + 1);
-        refine_row(e, a.hist + info.hist_off + (size_t)row.k * N, N, a.alpha, sm, sbuf);
+        const size_t h0 = info.hist_off + (size_t)row.k * N;
+        for (int j = threadIdx.x; j < N; j += blockDim.x) a.hist_last[h0 + j] = a.hist[h0 + j];
+        __syncthreads();
+        refine_row(e, a.hist + h0, N, a.alpha, sm, sbuf);
         if (a.staged32) {  // the float path's pairs of the new grid row
             __syncthreads();
             const FnConsts& fc = a.consts[row.b];
@@ -85,12 +90,12 @@ __global__ void __launch_bounds__(kPostThreads) batch_post_kernel(const PostArgs
 // Uniform grids e_l = l/N for every row, cleared histograms, accumulators,
 // logs and control words.
 __global__ void batch_init_kernel(double* edges, size_t n_edges, double* hist, size_t n_hist,
-                                  double* acc, size_t n_acc, double* log, size_t n_log,
-                                  unsigned* ctrl, int nbins) {
+                                  double* hist_last, double* acc, size_t n_acc, double* log,
+                                  size_t n_log, unsigned* ctrl, int nbins) {
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t nth = (size_t)gridDim.x * blockDim.x;
     for (size_t i = tid; i < n_edges; i += nth) edges[i] = (double)(i % (nbins + 1)) / nbins;
-    for (size_t i = tid; i < n_hist; i += nth) hist[i] = 0.0;
+    for (size_t i = tid; i < n_hist; i += nth) hist[i] = hist_last[i] = 0.0;
     for (size_t i = tid; i < n_acc; i += nth) acc[i] = 0.0;
     for (size_t i = tid; i < n_log; i += nth) log[i] = 0.0;
     for (size_t i = tid; i < (size_t)kCtrlWords; i += nth) ctrl[i] = 0u;
@@ -112,7 +117,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct BatchLayout {
-    size_t edges, hist, acc, log, consts, info, rows, tiles, ctrl, staged, total;
+    size_t edges, hist, hist_last, acc, log, consts, info, rows, tiles, ctrl, staged, total;
     size_t n_edges, n_hist, n_rows, max_tiles;
 };
 
@@ -140,6 +145,7 @@ BatchLayout batch_layout(int count, const int* dims, const uint64_t* n, int nbin
     size_t off = 0;
     L.edges = off; off = align_up(off + L.n_edges * sizeof(double));
     L.hist = off;  off = align_up(off + L.n_hist * sizeof(double));
+    L.hist_last = off; off = align_up(off + L.n_hist * sizeof(double));
     L.acc = off;   off = align_up(off + (size_t)count * 4 * sizeof(double));
     L.log = off;   off = align_up(off + (size_t)count * max_iters * kLogStride * sizeof(double));
     L.consts = off; off = align_up(off + (size_t)count * sizeof(FnConsts));
@@ -246,7 +252,8 @@ int launch_batch_init(vegas_batch* b) {
     const BatchLayout& L = b->L;
     const cudaError_t e = launch_kernel(
         batch_init_kernel, dim3(64), dim3(256), 0, b->stream, at<double>(b, L.edges), L.n_edges,
-        at<double>(b, L.hist), L.n_hist, at<double>(b, L.acc), (size_t)b->count * 4,
+        at<double>(b, L.hist), L.n_hist, at<double>(b, L.hist_last), at<double>(b, L.acc),
+        (size_t)b->count * 4,
         at<double>(b, L.log), (size_t)b->count * b->max_iters * kLogStride,
         at<unsigned>(b, L.ctrl), b->nbins);
     b->iters = 0;
@@ -497,6 +504,7 @@ int vegas_batch_iterate(vegas_batch* b, int adapt, double alpha) {
     pa.staged32 = a.staged32 ? at<float2>(b, L.staged) : nullptr;
     pa.edges = a.edges;
     pa.hist = a.hist;
+    pa.hist_last = at<double>(b, L.hist_last);
     pa.acc = a.acc;
     pa.log = at<double>(b, L.log);
     pa.ctrl = a.ctrl;
@@ -569,6 +577,18 @@ int vegas_batch_get_grid(vegas_batch* b, int index, double* host_edges) {
     if (!g.ok) return VEGAS_ECUDA;
     const size_t n = (size_t)b->dims[index] * (b->nbins + 1);
     if (cudaMemcpyAsync(host_edges, at<double>(b, b->L.edges) + b->info[index].edge_off,
+                        n * sizeof(double), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return VEGAS_ECUDA;
+    return VEGAS_OK;
+}
+
+int vegas_batch_get_histogram(vegas_batch* b, int index, double* host_hist) {
+    if (!b || !host_hist || index < 0 || index >= b->count) return VEGAS_EINVAL;
+    Dev g(b->device);
+    if (!g.ok) return VEGAS_ECUDA;
+    const size_t n = (size_t)b->dims[index] * b->nbins;
+    if (cudaMemcpyAsync(host_hist, at<double>(b, b->L.hist_last) + b->info[index].hist_off,
                         n * sizeof(double), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
         cudaStreamSynchronize(b->stream) != cudaSuccess)
         return VEGAS_ECUDA;

@@ -5,8 +5,8 @@
 // per-block partial sums, the last-block ticket and the (fJ)^2 histogram -- lives
 // in one file-scope device array.  Host code may not use that array's name as a
 // pointer (on the host it names a host-side stand-in, not device memory), so
-// each device's address of it is looked up once with cudaGetSymbolAddress, with
-// that device current, and passed to the kernels.
+// each call looks up the device's address of it with cudaGetSymbolAddress, with
+// that device current, and passes it to the kernels.
 #include <cfloat>
 #include <cmath>
 #include <cstring>
@@ -32,10 +32,18 @@ constexpr int kNaMaxDevices = 64;
 std::mutex g_setup_mutex;
 unsigned char* g_scratch_ptr[kNaMaxDevices] = {};
 
-// The device address of the scratch on `device` (current), looked up once.
-cudaError_t scratch_address(int device, unsigned char** out) {
+// The device address of the scratch on `device` (current).  A call made
+// outside stream capture looks it up afresh, so that an address left stale by a
+// context that was torn down and rebuilt (cudaDeviceReset) is never used; a
+// call made while `stream` is capturing reuses the last lookup on that device.
+cudaError_t scratch_address(int device, cudaStream_t stream, unsigned char** out) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusActive;
+    }
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[device]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_scratch_ptr[device]) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
@@ -193,11 +201,18 @@ extern "C" int vegas_iterate_noalloc(double* d_edges, int dim, int nbins, uint64
         cudaGetLastError();
         return VEGAS_EINVAL;
     }
+    // the result is written by the kernel: device memory on the grid's device
+    cudaPointerAttributes rattr;
+    if (cudaPointerGetAttributes(&rattr, d_result) != cudaSuccess ||
+        rattr.type != cudaMemoryTypeDevice || rattr.device != attr.device) {
+        cudaGetLastError();
+        return VEGAS_EINVAL;
+    }
     Guard g(attr.device);
     if (!g.ok) return VEGAS_ECUDA;
-    unsigned char* scratch = nullptr;
-    if (scratch_address(attr.device, &scratch) != cudaSuccess) return VEGAS_ECUDA;
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    unsigned char* scratch = nullptr;
+    if (scratch_address(attr.device, stream, &scratch) != cudaSuccess) return VEGAS_ECUDA;
 
     // Gaussian constants (Eq. 1), as for the workspace path
     NoAllocArgs a;

@@ -80,7 +80,40 @@ __global__ void shard_row_kernel(double* row, const double* totals, unsigned lon
     row[5] = var > 0.0 ? var : 0.0;
 }
 
+// The grid digest of vegas_grid_digest: sum over the edges i of
+// bits(e_i) K_i mod 2^64, K_i = splitmix64(i) | 1 (Vigna's SplitMix64 output
+// for the index), and its complement.  Unsigned sums wrap, so the order of the
+// additions does not matter: one block, a strided loop, a shuffle tree.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long i) {
+    unsigned long long z = (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void __launch_bounds__(256) grid_digest_kernel(const double* edges, int n,
+                                                          unsigned long long* out) {
+    __shared__ unsigned long long part[8];
+    unsigned long long h = 0ull;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        h += (unsigned long long)__double_as_longlong(edges[i]) * (splitmix64((unsigned)i) | 1ull);
+    for (int o = 16; o > 0; o >>= 1) h += __shfl_down_sync(0xffffffffu, h, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = h;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0ull;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        out[0] = t;
+        out[1] = ~t;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_grid_digest(const double* edges, int n, unsigned long long* out,
+                               cudaStream_t stream) {
+    return launch_kernel(grid_digest_kernel, dim3(1), dim3(256), 0, stream, edges, n, out);
+}
 
 cudaError_t launch_shard_row(double* row, const double* totals, unsigned long long n_total,
                              cudaStream_t stream) {

@@ -3,6 +3,7 @@
 // host-side combination of iterations.
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 
 #include <cuda_runtime.h>
@@ -228,6 +229,10 @@ using namespace vegas;
 namespace {
 
 constexpr size_t kAlign = 256;
+// pinned log staging of a state: the control words, then this many log rows
+constexpr int kPinnedLogRows = 4096;
+constexpr size_t kPinnedCtrlBytes = 256;
+static_assert(kCtrlWords * sizeof(unsigned) <= kPinnedCtrlBytes, "control words fit");
 
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -278,6 +283,32 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? VEGAS_OK : VEGAS_ECUD
 const void* kernel_for(const vegas_state* s, bool adapt) {
     return s->mode == VEGAS_FP32_EVAL ? iterate_kernel_f32(s->integrand, s->dim, adapt)
                                       : iterate_kernel_f64(s->integrand, s->dim, adapt);
+}
+
+// Resident blocks per SM of `kern` launched with (block, smem) on the state's
+// device (current): on the first use of that shape the kernel's dynamic
+// shared-memory limit is raised where needed and the occupancy queried; later
+// iterations read the answer from the state.
+cudaError_t launch_shape(vegas_state* s, const void* kern, int block, size_t smem, int* occ) {
+    for (int i = 0; i < s->n_shapes; ++i) {
+        const vegas_state::LaunchShape& c = s->shapes[i];
+        if (c.kern == kern && c.block == block && c.smem == smem) {
+            *occ = c.occ;
+            return cudaSuccess;
+        }
+    }
+    // static shared memory (~0.5 KB) counts against the 48 KB default as well
+    cudaError_t e = cudaSuccess;
+    if (smem > 40 * 1024)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int o = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, block, smem);
+    if (e != cudaSuccess) return e;
+    constexpr int kSlots = (int)(sizeof(s->shapes) / sizeof(s->shapes[0]));
+    const int slot = s->n_shapes < kSlots ? s->n_shapes++ : (s->next_shape++ % kSlots);
+    s->shapes[slot] = {kern, block, smem, o};
+    *occ = o;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -369,10 +400,26 @@ int vegas_init_grid(vegas_state** out, int dim, int nbins, uint64_t seed, int mo
     s->staged32 =
         mode == VEGAS_FP32_EVAL ? reinterpret_cast<float2*>(s->ws + L.staged) : nullptr;
 
+    // pinned staging for reading the log back: the control words and up to
+    // kPinnedLogRows rows (longer logs are read through it in pieces)
+    s->pin_rows = max_iters < kPinnedLogRows ? max_iters : kPinnedLogRows;
+    void* pin = nullptr;
+    if (cudaHostAlloc(&pin, kPinnedCtrlBytes + (size_t)s->pin_rows * kLogStride * sizeof(double),
+                      cudaHostAllocPortable) != cudaSuccess) {
+        delete s;
+        return VEGAS_ECUDA;
+    }
+    s->pin_ctrl = static_cast<unsigned*>(pin);
+    s->pin_rows_buf = reinterpret_cast<double*>(static_cast<unsigned char*>(pin) + kPinnedCtrlBytes);
+
     rc = cuda_status(launch_init(s->edges, s->hist, s->log, s->ctrl, dim, nbins, max_iters,
                                  s->stream));
     if (rc == VEGAS_OK) rc = restage(s);
-    if (rc != VEGAS_OK) { delete s; return rc; }
+    if (rc != VEGAS_OK) {
+        cudaFreeHost(pin);
+        delete s;
+        return rc;
+    }
     *out = s;
     return VEGAS_OK;
 }
@@ -429,16 +476,8 @@ static int enqueue_iteration(vegas_state* s, uint64_t begin, uint64_t end, int a
     if (user) {
         if (s->user.prepare(s->mode, ad ? 1 : 0, block, smem, &occ) != 0 || occ < 1)
             return VEGAS_ECUDA;
-    } else {
-        // static shared memory (~0.5 KB) counts against the 48 KB default as well
-        if (smem > 40 * 1024 &&
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                cudaSuccess)
-            return VEGAS_ECUDA;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) !=
-                cudaSuccess ||
-            occ < 1)
-            return VEGAS_ECUDA;
+    } else if (launch_shape(s, kern, block, smem, &occ) != cudaSuccess || occ < 1) {
+        return VEGAS_ECUDA;
     }
     const int bps = s->cfg.blocks_per_sm > 0 && s->cfg.blocks_per_sm < occ ? s->cfg.blocks_per_sm
                                                                            : occ;
@@ -575,6 +614,14 @@ int vegas_shard_import(vegas_state* s, const double* d_buf, uint64_t n_total) {
                                         n_total, s->stream));
 }
 
+int vegas_grid_digest(vegas_state* s, uint64_t* d_out) {
+    if (!s || !d_out || (reinterpret_cast<uintptr_t>(d_out) % 8) != 0) return VEGAS_EINVAL;
+    DeviceGuard g(s->device);
+    if (!g.ok) return VEGAS_ECUDA;
+    return cuda_status(launch_grid_digest(s->edges, s->dim * (s->nbins + 1),
+                                          reinterpret_cast<unsigned long long*>(d_out), s->stream));
+}
+
 int vegas_refine(vegas_state* s, double alpha) {
     vegas::TraceRange trace_("vegas_refine");
     if (!s || !(alpha >= 0.0) || !std::isfinite(alpha)) return VEGAS_EINVAL;
@@ -595,29 +642,43 @@ int vegas_refine(vegas_state* s, double alpha) {
     return cuda_status(launch_refine(r, s->stream));
 }
 
-static int read_log(vegas_state* s, double* rows, int max_rows, int* n_rows, int* nonfinite_any,
-                    int first) {
-    unsigned ctrl[kCtrlWords];
-    if (cudaMemcpyAsync(ctrl, s->ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, s->stream) !=
-        cudaSuccess)
+// The device's iteration count and the first min(count, max_rows) log rows,
+// read through the state's pinned staging: one copy and one stream
+// synchronisation for the control words, one each for the rows when they fit
+// the staging (longer logs go through it in pieces into `heap`).  *rows points
+// at the rows until the next read.
+static int read_log(vegas_state* s, int max_rows, const double** rows, int* n_rows,
+                    std::unique_ptr<double[]>* heap) {
+    if (cudaMemcpyAsync(s->pin_ctrl, s->ctrl, kCtrlWords * sizeof(unsigned),
+                        cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
         return VEGAS_ECUDA;
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return VEGAS_ECUDA;
-    if (ctrl[kStatus] & (kStatusLogFull | kStatusCheckFailed)) return VEGAS_ESTATE;
-    int n = (int)ctrl[kIter];
+    if (s->pin_ctrl[kStatus] & (kStatusLogFull | kStatusCheckFailed)) return VEGAS_ESTATE;
+    int n = (int)s->pin_ctrl[kIter];
     if (n > max_rows) n = max_rows;
-    if (n > 0) {
-        if (cudaMemcpyAsync(rows, s->log, (size_t)n * kLogStride * sizeof(double),
+    const size_t row_bytes = kLogStride * sizeof(double);
+    *rows = s->pin_rows_buf;
+    if (n > s->pin_rows) {
+        heap->reset(new (std::nothrow) double[(size_t)n * kLogStride]);
+        if (!*heap) return VEGAS_EINVAL;
+        *rows = heap->get();
+    }
+    for (int t0 = 0; t0 < n; t0 += s->pin_rows) {
+        const int m = n - t0 < s->pin_rows ? n - t0 : s->pin_rows;
+        if (cudaMemcpyAsync(s->pin_rows_buf, s->log + (size_t)t0 * kLogStride, m * row_bytes,
                             cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
             return VEGAS_ECUDA;
         if (cudaStreamSynchronize(s->stream) != cudaSuccess) return VEGAS_ECUDA;
+        if (*heap) std::memcpy(heap->get() + (size_t)t0 * kLogStride, s->pin_rows_buf, m * row_bytes);
     }
     *n_rows = n;
-    if (nonfinite_any) {
-        *nonfinite_any = 0;
-        for (int t = first; t < n; ++t)
-            if (rows[(size_t)t * kLogStride + 3] != 0.0) *nonfinite_any = 1;
-    }
     return VEGAS_OK;
+}
+
+static bool any_nonfinite(const double* rows, int first, int end) {
+    for (int t = first; t < end; ++t)
+        if (rows[(size_t)t * kLogStride + 3] != 0.0) return true;
+    return false;
 }
 
 int vegas_result(vegas_state* s, int first_iter, double* mean, double* sigma, double* chi2_dof,
@@ -626,19 +687,18 @@ int vegas_result(vegas_state* s, int first_iter, double* mean, double* sigma, do
     if (!s || first_iter < 0) return VEGAS_EINVAL;
     DeviceGuard g(s->device);
     if (!g.ok) return VEGAS_ECUDA;
-    double* rows = new (std::nothrow) double[(size_t)s->max_iters * kLogStride];
-    if (!rows) return VEGAS_EINVAL;
-    int n = 0, bad = 0;
-    int rc = read_log(s, rows, s->max_iters, &n, &bad, first_iter);
-    if (rc != VEGAS_OK) { delete[] rows; return rc; }
+    const double* rows = nullptr;
+    std::unique_ptr<double[]> heap;
+    int n = 0;
+    const int rc = read_log(s, s->max_iters, &rows, &n, &heap);
+    if (rc != VEGAS_OK) return rc;
     if (n_iter) *n_iter = n;
     double m = NAN, sg = NAN, c2 = NAN;
     combine_rows(rows, kLogStride, first_iter, n, &m, &sg, &c2);
-    delete[] rows;
     if (mean) *mean = m;
     if (sigma) *sigma = sg;
     if (chi2_dof) *chi2_dof = c2;
-    return bad ? VEGAS_ENONFINITE : VEGAS_OK;
+    return any_nonfinite(rows, first_iter, n) ? VEGAS_ENONFINITE : VEGAS_OK;
 }
 
 int vegas_result_range(vegas_state* s, int first_iter, int end_iter, double* mean,
@@ -646,56 +706,49 @@ int vegas_result_range(vegas_state* s, int first_iter, int end_iter, double* mea
     if (!s || first_iter < 0 || end_iter <= first_iter) return VEGAS_EINVAL;
     DeviceGuard g(s->device);
     if (!g.ok) return VEGAS_ECUDA;
-    double* rows = new (std::nothrow) double[(size_t)s->max_iters * kLogStride];
-    if (!rows) return VEGAS_EINVAL;
-    int n = 0, bad = 0;
-    int rc = read_log(s, rows, s->max_iters, &n, nullptr, first_iter);
-    if (rc == VEGAS_OK && end_iter > n) rc = VEGAS_EINVAL;  // not logged (yet)
-    if (rc == VEGAS_OK) {
-        for (int t = first_iter; t < end_iter; ++t)
-            if (rows[(size_t)t * kLogStride + 3] != 0.0) bad = 1;
-        double m = NAN, sg = NAN, c2 = NAN;
-        combine_rows(rows, kLogStride, first_iter, end_iter, &m, &sg, &c2);
-        if (mean) *mean = m;
-        if (sigma) *sigma = sg;
-        if (chi2_dof) *chi2_dof = c2;
-    }
-    delete[] rows;
-    return rc != VEGAS_OK ? rc : (bad ? VEGAS_ENONFINITE : VEGAS_OK);
+    const double* rows = nullptr;
+    std::unique_ptr<double[]> heap;
+    int n = 0;
+    const int rc = read_log(s, s->max_iters, &rows, &n, &heap);
+    if (rc != VEGAS_OK) return rc;
+    if (end_iter > n) return VEGAS_EINVAL;  // not logged (yet)
+    double m = NAN, sg = NAN, c2 = NAN;
+    combine_rows(rows, kLogStride, first_iter, end_iter, &m, &sg, &c2);
+    if (mean) *mean = m;
+    if (sigma) *sigma = sg;
+    if (chi2_dof) *chi2_dof = c2;
+    return any_nonfinite(rows, first_iter, end_iter) ? VEGAS_ENONFINITE : VEGAS_OK;
 }
 
 int vegas_get_iterations(vegas_state* s, double* host_rows, int max_rows, int* n_rows) {
     if (!s || !host_rows || max_rows < 0 || !n_rows) return VEGAS_EINVAL;
+    *n_rows = 0;
     DeviceGuard g(s->device);
     if (!g.ok) return VEGAS_ECUDA;
-    double* rows = new (std::nothrow) double[(size_t)s->max_iters * kLogStride];
-    if (!rows) return VEGAS_EINVAL;
+    const double* rows = nullptr;
+    std::unique_ptr<double[]> heap;
     int n = 0;
-    const int rc = read_log(s, rows, max_rows < s->max_iters ? max_rows : s->max_iters, &n,
-                            nullptr, 0);
-    if (rc == VEGAS_OK)
-        for (int t = 0; t < n; ++t)
-            for (int c = 0; c < 6; ++c)
-                host_rows[(size_t)t * 6 + c] = rows[(size_t)t * kLogStride + c];
-    *n_rows = rc == VEGAS_OK ? n : 0;
-    delete[] rows;
-    return rc;
+    const int rc = read_log(s, max_rows < s->max_iters ? max_rows : s->max_iters, &rows, &n, &heap);
+    if (rc != VEGAS_OK) return rc;
+    for (int t = 0; t < n; ++t)
+        for (int c = 0; c < 6; ++c) host_rows[(size_t)t * 6 + c] = rows[(size_t)t * kLogStride + c];
+    *n_rows = n;
+    return VEGAS_OK;
 }
 
 int vegas_get_iteration_times(vegas_state* s, double* host_ns, int max_rows, int* n_rows) {
     if (!s || !host_ns || max_rows < 0 || !n_rows) return VEGAS_EINVAL;
+    *n_rows = 0;
     DeviceGuard g(s->device);
     if (!g.ok) return VEGAS_ECUDA;
-    double* rows = new (std::nothrow) double[(size_t)s->max_iters * kLogStride];
-    if (!rows) return VEGAS_EINVAL;
+    const double* rows = nullptr;
+    std::unique_ptr<double[]> heap;
     int n = 0;
-    const int rc = read_log(s, rows, max_rows < s->max_iters ? max_rows : s->max_iters, &n,
-                            nullptr, 0);
-    if (rc == VEGAS_OK)
-        for (int t = 0; t < n; ++t) host_ns[t] = rows[(size_t)t * kLogStride + 6];
-    *n_rows = rc == VEGAS_OK ? n : 0;
-    delete[] rows;
-    return rc;
+    const int rc = read_log(s, max_rows < s->max_iters ? max_rows : s->max_iters, &rows, &n, &heap);
+    if (rc != VEGAS_OK) return rc;
+    for (int t = 0; t < n; ++t) host_ns[t] = rows[(size_t)t * kLogStride + 6];
+    *n_rows = n;
+    return VEGAS_OK;
 }
 
 int vegas_get_grid(vegas_state* s, double* host_edges) {
@@ -746,6 +799,7 @@ int vegas_destroy(vegas_state* s) {
     {
         DeviceGuard g(s->device);
         if (g.ok && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = VEGAS_ECUDA;
+        if (s->pin_ctrl && cudaFreeHost(s->pin_ctrl) != cudaSuccess) rc = VEGAS_ECUDA;
     }
     delete s;
     return rc;

@@ -134,6 +134,9 @@ void combine_rows(const double* rows, int stride, int first_iter, int n, double*
 // for n_total samples.
 cudaError_t launch_shard_row(double* row, const double* totals, unsigned long long n_total,
                              cudaStream_t stream);
+// The 64-bit digest of n edges and its complement into out[0], out[1].
+cudaError_t launch_grid_digest(const double* edges, int n, unsigned long long* out,
+                               cudaStream_t stream);
 cudaError_t launch_init(double* edges, double* hist, double* log, unsigned* ctrl, int dim,
                         int nbins, int max_iters, cudaStream_t stream);
 
@@ -165,6 +168,22 @@ struct vegas_state {
     double box_lo[VEGAS_MAX_DIM], box_hi[VEGAS_MAX_DIM];
     int inject_countdown;  // vegas_inject_failure: fail the n-th next enqueueing call (0: off)
     int smem_optin;        // dynamic shared memory one block may use on this device
+    // Launch shapes already prepared on this state's device: the kernel's
+    // dynamic shared-memory limit raised where needed and its resident blocks
+    // per SM queried once per (kernel, block, shared bytes), not per iteration.
+    struct LaunchShape {
+        const void* kern;
+        int block;
+        size_t smem;
+        int occ;
+    } shapes[8];
+    int n_shapes, next_shape;
+    // Pinned host staging owned by the descriptor (cudaHostAlloc at creation,
+    // cudaFreeHost in vegas_destroy): the control words, then up to pin_rows
+    // log rows; every read of the log goes through it.
+    unsigned* pin_ctrl;
+    double* pin_rows_buf;
+    int pin_rows;
 };
 
 // vegas_inject_failure's check, at the start of every enqueueing call: true

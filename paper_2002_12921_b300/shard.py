@@ -9,15 +9,50 @@ never diverge and the result equals a single device's run up to the order of
 the sums.  (VegasFlow Sec. 3.4 distributes events over devices of one
 machine; this is that split, written for counter-based sampling.)
 
+Identical grids rest on every rank receiving bit-identical totals from the
+all-reduce.  ``ShardedVegas`` checks that they did: after every
+``check_every``-th refinement (and on request) each rank reduces a 64-bit digest
+of its grid's bit patterns with MAX, paired with its complement (so one
+16-byte all-reduce gives the largest and the smallest digest), and every rank
+raises ``GridMismatch`` when they differ.  Cost per check: one digest kernel,
+one 16-byte all-reduce and one host read of its result (a stream
+synchronisation).
+
 An engine is what one rank computes with; it provides
     iterate_range(n, begin, end, adapt), export() -> 1-d tensor,
-    import_(totals, n), refine(alpha), rows(), grid().
+    import_(totals, n), refine(alpha), rows(), grid(),
+    grid_digest() -> int64 tensor [digest, ~digest] on the collective's device.
 ``GpuShardEngine`` wraps a CUDA ``Vegas`` state (vegas_iterate_range /
-vegas_shard_export / vegas_shard_import); tests plug in CPU engines.
+vegas_shard_export / vegas_shard_import / vegas_grid_digest); tests plug in
+CPU engines.
 """
 import logging
 
+import numpy as np
+
 log = logging.getLogger(__name__)
+
+_M64 = (1 << 64) - 1
+
+
+def _splitmix64(i):
+    """Vigna's SplitMix64 output function of the uint64 array i."""
+    with np.errstate(over="ignore"):
+        z = (i + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def grid_digest_host(edges):
+    """The digest vegas_grid_digest defines, of a host grid (dim x (nbins+1)
+    doubles, row-major): sum_i bits(e_i) (splitmix64(i) | 1) mod 2^64, as a
+    signed 64-bit pair [digest, ~digest]."""
+    bits = np.ascontiguousarray(edges, dtype=np.float64).ravel().view(np.uint64)
+    k = _splitmix64(np.arange(bits.size, dtype=np.uint64)) | np.uint64(1)
+    with np.errstate(over="ignore"):
+        h = int(np.sum(bits * k, dtype=np.uint64))
+    return np.array([h, ~h & _M64], dtype=np.uint64).view(np.int64)
 
 
 def shard_range(n, rank, world):
@@ -36,6 +71,7 @@ class GpuShardEngine:
         self.v, self.B = vegas, B
         self.buf = torch.zeros(3 + vegas.dim * vegas.nbins, dtype=torch.float64,
                                device=vegas.workspace.device)
+        self.digest = torch.zeros(2, dtype=torch.int64, device=vegas.workspace.device)
 
     def iterate_range(self, n, begin, end, adapt):
         rc = self.B.lib().vegas_iterate_range(self.v.handle, int(n), int(begin), int(end),
@@ -71,19 +107,36 @@ class GpuShardEngine:
     def grid(self):
         return self.v.grid()
 
+    def grid_digest(self):
+        self.B._check(self.B.lib().vegas_grid_digest(self.v.handle, self.digest.data_ptr()),
+                      "vegas_grid_digest")
+        return self.digest
+
+
+class RankFailure(RuntimeError):
+    """Raised (host side) by a rank that could not produce its share."""
+
+
+class GridMismatch(RankFailure):
+    """Raised on every rank when the ranks' grids differ after a refinement."""
+
 
 class ShardedVegas:
     """Drives one engine per rank of a torch.distributed process group: each
     iteration computes this rank's index range, all-reduces the partial sums
     (NCCL for CUDA tensors, gloo for CPU ones) and refines.  Every iteration
-    needs n >= world size."""
+    needs n >= world size.  check_every = k > 0: after every k-th adapting
+    iteration the ranks compare grid digests (check_grids); 0: only when
+    check_grids() is called (run() calls it at the end)."""
 
-    def __init__(self, engine, group=None):
+    def __init__(self, engine, group=None, check_every=1):
         import torch.distributed as dist
 
         self.engine, self.group, self.dist = engine, group, dist
         self.rank = dist.get_rank(group) if dist.is_initialized() else 0
         self.world = dist.get_world_size(group) if dist.is_initialized() else 1
+        self.check_every = check_every
+        self.refinements = 0
 
     def iterate(self, n, adapt, alpha=1.5):
         if n < self.world:
@@ -96,14 +149,27 @@ class ShardedVegas:
         self.engine.import_(totals, n)
         if adapt:
             self.engine.refine(alpha)
+            self.refinements += 1
+            if self.check_every and self.refinements % self.check_every == 0:
+                self.check_grids()
+
+    def check_grids(self):
+        """Raise GridMismatch (on every rank) unless all ranks' grids have the
+        same digest: one all-reduce of [digest, ~digest] with MAX gives the
+        largest digest and the complement of the smallest."""
+        d = self.engine.grid_digest()
+        if self.world > 1:
+            d = d.clone()
+            self.dist.all_reduce(d, op=self.dist.ReduceOp.MAX, group=self.group)
+        hi, lo = int(d[0]), ~int(d[1])
+        if hi != lo:
+            raise GridMismatch(f"rank {self.rank}: grids differ across ranks after "
+                               f"{self.refinements} refinements (digests {lo:#x} .. {hi:#x})")
 
     def run(self, schedule, alpha=1.5):
         for n, adapt in schedule:
             self.iterate(n, adapt, alpha)
-
-
-class RankFailure(RuntimeError):
-    """Raised (host side) by a rank that could not produce its share."""
+        self.check_grids()
 
 
 class VirtualRanks:
@@ -146,6 +212,11 @@ class VirtualRanks:
             eng.import_(totals, n)
             if adapt:
                 eng.refine(alpha)
+        if adapt:
+            digests = {tuple(int(x) for x in eng.grid_digest()) for eng in self.engines}
+            if len(digests) != 1:
+                raise GridMismatch(f"virtual ranks' grids differ after iteration "
+                                   f"{self.iteration}")
         self.iteration += 1
 
     def run(self, schedule, alpha=1.5):

@@ -13,7 +13,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 import oracle  # noqa: E402
-from paper_2002_12921_b300.shard import ShardedVegas  # noqa: E402
+from paper_2002_12921_b300.shard import ShardedVegas, grid_digest_host  # noqa: E402
 
 
 class OracleEngine:
@@ -54,22 +54,44 @@ class OracleEngine:
     def grid(self):
         return self.e
 
+    def grid_digest(self):
+        return torch.from_numpy(grid_digest_host(self.e))
 
-def gloo_worker(rank, world, port, out_dir, spec, fail_rank, fail_iter):
+
+class PerturbingEngine(OracleEngine):
+    """An oracle engine whose refinement after iteration `at` moves one
+    interior edge by one ulp (a rank that received different totals)."""
+
+    def __init__(self, *args, at=1, edge=(0, 3)):
+        super().__init__(*args)
+        self.at, self.edge = at, edge
+
+    def refine(self, alpha):
+        super().refine(alpha)
+        if self.it - 1 == self.at:
+            self.e = self.e.copy()
+            self.e[self.edge] = np.nextafter(self.e[self.edge], 2.0)
+
+
+def gloo_worker(rank, world, port, out_dir, spec, fail_rank, fail_iter, perturb_rank=-1):
     """One gloo rank: run the sharded schedule and save rows and grid; the rank
     `fail_rank` raises (host side) before its share of iteration `fail_iter`;
-    the others record the error their next collective reports."""
+    the others record the error their next collective reports.  The rank
+    `perturb_rank` moves one edge of its grid by one ulp after the refinement
+    of iteration 1 (every rank must then raise GridMismatch)."""
     import torch.distributed as dist
 
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
                             world_size=world, timeout=timedelta(seconds=20))
-    eng = OracleEngine(*spec["engine"])
+    eng = (PerturbingEngine(*spec["engine"], at=1) if rank == perturb_rank
+           else OracleEngine(*spec["engine"]))
     sv = ShardedVegas(eng)
     try:
         for t, (n, adapt) in enumerate(spec["schedule"]):
             if rank == fail_rank and t == fail_iter:
                 raise RuntimeError("injected failure")
             sv.iterate(n, adapt, spec["alpha"])
+        sv.check_grids()
         np.save(os.path.join(out_dir, f"rows{rank}.npy"), eng.rows())
         np.save(os.path.join(out_dir, f"grid{rank}.npy"), eng.grid())
     except Exception:

@@ -59,8 +59,40 @@ def test_batch_fp64_matches_single_integral_oracle_runs():
             assert abs(log[b, t, 4] - o["log"][t]["I"]) <= tol * abs(o["log"][t]["I"]), (b, t)
             assert abs(log[b, t, 5] - o["log"][t]["var"]) <= 100 * tol * o["log"][t]["var"]
         assert np.allclose(B.grid(b), o["edges"], rtol=1e-12, atol=1e-15)
+        # the histogram the last refinement used (iteration 2), bin by bin
+        htol = max(1e-11, 2 * fp64_tol(o["grids"][2]))
+        assert np.allclose(B.histogram(b), o["log"][2]["hist"], rtol=htol, atol=0), b
         m, s, c, k, bad = B.result(b)
         assert k == iters and not bad
+    B.close()
+
+
+@pytest.mark.parametrize("tile", [0, 4096])
+def test_batch_fp32_histograms_bin_by_bin_against_the_oracle(tile):
+    """FP32 tiles of the persistent kernel: the (f J)^2 histogram each
+    integral's first refinement used (uniform grid, same counters) equals the
+    oracle's bin by bin within the float budget of one bin, and the refined
+    grid equals the oracle's refinement of its own histogram within what that
+    budget lets a refinement move.  The widest integral (d = 20 at N = 30, 600
+    bins) misses the default 52 KB budget for 32 copies, so the round runs as
+    one 768-thread block per SM, every tile with lane-owned copies; tile 4096
+    spreads one integral's samples over many tiles, each flushed on its own."""
+    from tests.fp32_budget import assert_hist_close, fp32_hist_tol, refine_edge_tol
+
+    dims, ns, params = small_batch()
+    B = V.VegasBatch(dims, ns, 30, 7, V.VEGAS_FP32_EVAL, params, max_iters=4)
+    if tile:
+        B.config(tile_samples=tile)
+    B.reset()
+    B.iterate(adapt=True)
+    for b, (d, n, p) in enumerate(zip(dims, ns, params)):
+        e = oracle.uniform_grid(d, 30)
+        o = oracle.iterate(e, 7, 0, n, W.GAUSS, p, True, integral_id=b, nthreads=4)
+        rt, at = fp32_hist_tol(W.GAUSS, d, p, e, min(n, tile or 65536), copies=32, sms=1,
+                               block=768)
+        assert_hist_close(B.histogram(b), o["hist"], rt, at, f"integral {b} (d={d})")
+        etol = refine_edge_tol(e, o["hist"], 1.5, rt)
+        assert np.allclose(B.grid(b), oracle.refine(e, o["hist"], 1.5), rtol=0, atol=etol), b
     B.close()
 
 

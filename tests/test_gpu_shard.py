@@ -91,3 +91,26 @@ def test_a_failed_launch_is_retried_and_the_run_stays_exact():
     v.run([(10_000, 1), (10_000, 0)])  # the state is untouched and usable
     assert v.result(0)[3] == 2
     v.close()
+
+
+@pytest.mark.parametrize("mode", [V.VEGAS_FP64, V.VEGAS_FP32_EVAL])
+def test_grid_digest_on_the_device_equals_its_host_definition(mode):
+    """vegas_grid_digest (a kernel over the grid in device memory) equals the
+    host digest of the same grid read back, on a uniform and on a refined
+    grid; the pair's second word is the complement of the first; the virtual
+    ranks' digests agree after every refinement."""
+    from paper_2002_12921_b300.shard import grid_digest_host
+
+    v = V.Vegas(6, 40, 21, mode, W.GAUSS, P, max_iters=4)
+    eng = GpuShardEngine(v)
+    for _ in range(2):
+        d = eng.grid_digest().cpu().numpy().copy()
+        assert np.array_equal(d, grid_digest_host(v.grid()))
+        assert int(d[1]) == ~int(d[0])
+        v.iterate(200_000, 1)
+        v.refine(1.5)
+    v.close()
+    states = [V.Vegas(6, 40, 21, mode, W.GAUSS, P, max_iters=8) for _ in range(2)]
+    VirtualRanks([GpuShardEngine(s) for s in states]).run(SCHED)  # digests checked inside
+    for s in states:
+        s.close()

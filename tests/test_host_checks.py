@@ -31,7 +31,11 @@ def test_algorithmic_counts():
     assert bench.products_per_sample(8) == 42
     assert bench.products_per_sample(16) == 2 + 64 + 16
     assert bench.products_per_sample(1) == 2 + 16 + 1
-    assert bench.alg_ops_per_sample(8) == 167
+    # the method's count: Philox 60 per call, 7 per dimension, 12 per sample
+    assert bench.alg_ops_per_sample(8) == 120 + 56 + 12 == 188
+    assert bench.alg_ops_per_sample(16) == 240 + 112 + 12
+    # the kernel's count, round keys computed once per launch
+    assert bench.kernel_ops_per_sample(8) == 167
     assert bench.SAMPLES_PER_STEP == 10 * 10_000_000 + 5 * 100_000_000
 
 

@@ -270,3 +270,39 @@ def test_vegas_over_a_box_reaches_the_erf_closed_form():
     r = oracle.run(3, 40, 11, W.GAUSS, W.gauss_params(3, a, mu), [(100_000, 1)] * 6,
                    nthreads=4, first_iter=2, box=box)
     assert abs(r["mean"] - exact) < 5 * r["sigma"] and r["sigma"] < 1e-3 * exact
+
+
+# ------------------------------------------- the d=16 two-peak mixture (config 5)
+def mix_locking_run(seed, n=500_000, iters=15):
+    """The d=16 mixture of the Eq. 1 Gaussian at centres 1/3 and 2/3 (a = 0.1,
+    100 bins) at a reduced sample count per iteration, every iteration
+    adapting; returns the oracle's run."""
+    return oracle.run(16, 100, seed, W.GAUSS_MIX2, W.mix2_params(16, 0.1), [(n, 1)] * iters,
+                      nthreads=8)
+
+
+@pytest.mark.parametrize("seed", [5, 6, 7, 8])
+def test_separable_grid_locks_onto_one_peak_of_the_d16_mixture(seed):
+    """The Vegas grid is a product of one-dimensional maps (Lepage 1978 Sec.
+    3), so it cannot put density at both diagonal peaks (1/3, ..., 1/3) and
+    (2/3, ..., 2/3) without also covering the 2^16 - 2 empty corners between
+    them; the refinement's feedback makes one peak win.  The FP64 oracle on
+    config 5's shape: after 15 adapting iterations of 5e5 samples every
+    dimension's grid holds >= 75 of its 100 bins within 0.1 of the same
+    centre and <= 3 near the other, and the estimate combined over the last 5
+    iterations is within 4 sigma of half the integral, J(1/3)^16 / 2, and
+    hundreds of sigma from the full one, J(1/3)^16 (J(c) the one-dimensional
+    erf integral; J(1/3) = J(2/3) by symmetry)."""
+    a = 0.1
+    J = 0.5 * (erf((1 - 1 / 3) / a) + erf((1 / 3) / a))
+    full, half = J ** 16, 0.5 * J ** 16
+    r = mix_locking_run(seed)
+    e = r["edges"]
+    mids = 0.5 * (e[:, 1:] + e[:, :-1])
+    near = np.stack([(np.abs(mids - c) < 0.1).sum(axis=1) for c in (1 / 3, 2 / 3)])
+    won = int(np.argmax(near.sum(axis=1)))
+    assert np.all(near[won] >= 75), near
+    assert np.all(near[1 - won] <= 3), near
+    m, s, _ = oracle.combine([x["I"] for x in r["log"][10:]], [x["var"] for x in r["log"][10:]])
+    assert abs(m - half) < 4 * s, (m, s, half)
+    assert (full - m) > 300 * s, (m, s, full)

@@ -9,8 +9,9 @@ import torch
 
 import oracle
 from paper_2002_12921_b300 import workloads as W
-from paper_2002_12921_b300.shard import RankFailure, VirtualRanks, shard_range
-from tests.shard_workers import OracleEngine, gloo_worker
+from paper_2002_12921_b300.shard import (GridMismatch, RankFailure, VirtualRanks,
+                                         grid_digest_host, shard_range)
+from tests.shard_workers import OracleEngine, PerturbingEngine, gloo_worker
 
 P = W.gauss_params(3, 0.15, [0.4, 0.5, 0.6])
 SCHED = [(30_000, 1), (30_000, 1), (20_000, 1), (40_001, 0)]
@@ -73,12 +74,12 @@ def _port():
         return s.getsockname()[1]
 
 
-def _spawn(tmp_path, fail_rank=-1, fail_iter=-1):
+def _spawn(tmp_path, fail_rank=-1, fail_iter=-1, perturb_rank=-1):
     spec = {"engine": (3, 20, 4, W.GAUSS, P), "schedule": SCHED, "alpha": 1.5}
     ctx = torch.multiprocessing.get_context("spawn")
     port = _port()
     procs = [ctx.Process(target=gloo_worker, args=(r, 2, port, str(tmp_path), spec, fail_rank,
-                                                   fail_iter)) for r in range(2)]
+                                                   fail_iter, perturb_rank)) for r in range(2)]
     for p in procs:
         p.start()
     for p in procs:
@@ -106,3 +107,56 @@ def test_gloo_rank_failure_is_detected_by_its_peer(tmp_path):
     assert codes[1] == 3
     assert os.path.exists(tmp_path / "error0.txt")
     assert not os.path.exists(tmp_path / "rows0.npy")
+
+
+def test_gloo_grids_that_differ_by_one_ulp_are_detected(tmp_path):
+    """Rank 1's grid moves by one ulp in one edge after the second refinement
+    (as if its totals had differed): the digest check after that refinement
+    raises GridMismatch on both ranks, before either runs another iteration."""
+    codes = _spawn(tmp_path, perturb_rank=1)
+    assert codes == [0, 0]
+    for r in range(2):
+        err = (tmp_path / f"error{r}.txt").read_text()
+        assert "GridMismatch" in err and "after 2 refinements" in err, err
+        assert not os.path.exists(tmp_path / f"rows{r}.npy")
+
+
+def test_virtual_ranks_detect_a_diverged_grid():
+    engines = [OracleEngine(3, 20, 4, W.GAUSS, P), PerturbingEngine(3, 20, 4, W.GAUSS, P, at=0)]
+    with pytest.raises(GridMismatch):
+        VirtualRanks(engines).run(SCHED)
+
+
+def _digest_by_definition(edges):
+    """sum_i bits(e_i) (splitmix64(i) | 1) mod 2^64 with Python integers, where
+    splitmix64(i) is output i of Vigna's SplitMix64 generator run as published:
+    a 64-bit state starting at 0, advanced by the golden-ratio increment
+    before each output is mixed."""
+    m = (1 << 64) - 1
+    bits = np.ascontiguousarray(edges, dtype=np.float64).ravel().view(np.uint64)
+    state, total = 0, 0
+    for b in bits:
+        state = (state + 0x9E3779B97F4A7C15) & m
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+        z ^= z >> 31
+        total = (total + int(b) * (z | 1)) & m
+    return total
+
+
+def test_grid_digest_definition_and_sensitivity():
+    """The host digest equals its definition computed with Python integers
+    and the generator run step by step; equal grids give equal digests; moving
+    any single edge by one ulp changes the digest."""
+    e = oracle.refine(oracle.uniform_grid(3, 20), np.arange(60.0).reshape(3, 20) + 1.0, 1.5)
+    d = grid_digest_host(e)
+    h = _digest_by_definition(e)
+    assert int(d[0]) & ((1 << 64) - 1) == h
+    assert int(d[1]) == ~int(d[0])
+    assert np.array_equal(grid_digest_host(e.copy()), d)
+    for k in range(3):
+        for j in range(21):
+            f = e.copy()
+            f[k, j] = np.nextafter(f[k, j], 2.0)
+            assert grid_digest_host(f)[0] != d[0], (k, j)
