@@ -1,6 +1,8 @@
 // Instantiates the big-block adapting iterate kernel (float arithmetic, one
-// block of up to kBigBlockThreads per SM) for the VEGAS_GAUSS integrand, dimensions
+// block of up to kBigBlockThreads per SM) and the default-shape one with the
+// run-time histogram copy count for the VEGAS_GAUSS integrand, dimensions
 // 1..20.
 #include "iterate_kernel.cuh"
 
 VEGAS_KERNEL_TABLE_BIG(iterate_table_big_f32_gauss, VEGAS_GAUSS)
+VEGAS_KERNEL_TABLE_FEW(iterate_table_few_f32_gauss, VEGAS_GAUSS)

@@ -365,7 +365,8 @@ __device__ __forceinline__ void stage_grid(const double* __restrict__ edges, int
 // The samples [first, end) with step `stride` of iteration `it`: Philox words
 // (the first two rounds shared by a sample's calls), grid map, and the
 // integrand F in its staged coordinate; each sample's weight f J, the
-// integrand state and the bins go to sink(fw, f, bins).  Returns whether the
+// integrand state and its bins go to sink(fw, f, bins), bins[k] = k N + j_k
+// (the bin's index in the staged grid and in the histogram).  Returns whether the
 // debug build's per-sample checks held (bin index < N, mapped coordinate
 // finite); always true in the release build.
 template <typename R, int D, typename F, typename Sink>
@@ -415,14 +416,15 @@ __device__ __forceinline__ bool sample_loop(unsigned long long first, unsigned l
                 if (k < D) {
                     const uint32_t j = __umulhi(w[t], (uint32_t)N);
                     const uint32_t l = w[t] * (uint32_t)N;
-                    const Pair g = sgrid[k * N + j];
+                    const int gi = k * N + (int)j;
+                    const Pair g = sgrid[gi];
                     const R x = P::fma(P::unit(l), g.y, g.x);
 #ifdef VEGAS_DEBUG_CHECKS
                     checks_ok &= j < (uint32_t)N && P::finite(x);
 #endif
                     J *= g.y;
                     f.add(k, x, fc);
-                    if (Sink::kNeedBins) bins[k] = j;
+                    if (Sink::kNeedBins) bins[k] = (uint32_t)gi;
                 }
             }
             if (sizeof(R) == 4) J *= (4 * q + 4 <= D) ? n4 : nlast;
@@ -477,16 +479,23 @@ struct HistBits<double> {
     }
 };
 
-template <typename R, int D, bool ADAPT>
+// LOGR >= 0: 2^LOGR copies known at compile time (the address of a bin's copy
+// is then one shift-and-add of the bin index); -1: the run-time count lr.
+template <typename R, int D, bool ADAPT, int LOGR = -1>
 struct IterateSink {
     static constexpr bool kNeedBins = ADAPT;
     using H = typename Prec<R>::Hist;
     Acc<R> acc;
     unsigned bad = 0;
-    H* shist;
-    int N, logr, lane_copy;
-    __device__ __forceinline__ IterateSink(H* h, int n, int lr)
-        : shist(h), N(n), logr(lr), lane_copy(threadIdx.x & ((1 << lr) - 1)) {}
+    H* hlane;  // this lane's copy: the histogram's base plus the lane's copy index
+    int logr;
+    __device__ __forceinline__ IterateSink(H* h, int, int lr)
+        : hlane(h + (threadIdx.x & ((1 << (LOGR >= 0 ? LOGR : lr)) - 1))),
+          logr(LOGR >= 0 ? LOGR : lr) {}
+    // the word of bin index i (= k N + j) in this lane's copy
+    __device__ __forceinline__ H* at(uint32_t i) const {
+        return hlane + ((int)i << (LOGR >= 0 ? LOGR : logr));
+    }
     template <typename F>
     __device__ __forceinline__ void operator()(R fw, const F&, const uint32_t (&bins)[D]) {
         if (Prec<R>::finite(fw)) {
@@ -506,32 +515,32 @@ struct IterateSink {
                     // keep the plain atomic add: the FP64 kernels are bound by
                     // the FP64 pipe, and grouping measured no faster there.)
                     using B = typename HistBits<H>::type;
-                    B* su = reinterpret_cast<B*>(shist);
 #pragma unroll
                     for (int k0 = 0; k0 < D; k0 += 4) {
                         constexpr int G = 4;
+                        H* p[G];
                         H old[G];
 #pragma unroll
                         for (int g = 0; g < G; ++g)
-                            if (k0 + g < D)
-                                old[g] = shist[(((k0 + g) * N + (int)bins[k0 + g]) << logr) | lane_copy];
+                            if (k0 + g < D) {
+                                p[g] = at(bins[k0 + g]);
+                                old[g] = *p[g];
+                            }
                         B got[G];
 #pragma unroll
                         for (int g = 0; g < G; ++g)
                             if (k0 + g < D)
-                                got[g] = atomicCAS(
-                                    &su[(((k0 + g) * N + (int)bins[k0 + g]) << logr) | lane_copy],
-                                    HistBits<H>::bits(old[g]), HistBits<H>::bits(old[g] + (H)fw2));
+                                got[g] = atomicCAS(reinterpret_cast<B*>(p[g]),
+                                                   HistBits<H>::bits(old[g]),
+                                                   HistBits<H>::bits(old[g] + (H)fw2));
 #pragma unroll
                         for (int g = 0; g < G; ++g)
                             if (k0 + g < D && got[g] != HistBits<H>::bits(old[g]))
-                                atomicAdd(&shist[(((k0 + g) * N + (int)bins[k0 + g]) << logr) | lane_copy],
-                                          (H)fw2);
+                                atomicAdd(p[g], (H)fw2);
                     }
                 } else {
 #pragma unroll
-                    for (int k = 0; k < D; ++k)
-                        atomicAdd(&shist[((k * N + (int)bins[k]) << logr) | lane_copy], (H)fw2);
+                    for (int k = 0; k < D; ++k) atomicAdd(at(bins[k]), (H)fw2);
                 }
             }
         } else {
@@ -578,7 +587,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // The kernel body.  R = float or double, D = dimension, F = integrand type,
 // ADAPT = accumulate the refinement histogram.
 // ------------------------------------------------------------------------
-template <typename R, int D, typename F, bool ADAPT>
+template <typename R, int D, typename F, bool ADAPT, int LOGR = -1>
 __device__ __forceinline__ void iterate_body(const IterArgs& a) {
     using P = Prec<R>;
     using Pair = typename P::Pair;
@@ -590,7 +599,7 @@ __device__ __forceinline__ void iterate_body(const IterArgs& a) {
     __shared__ int s_last;
 
     const int N = a.nbins;
-    const int logr = ADAPT ? a.hist_log2r : 0;
+    const int logr = ADAPT ? (LOGR >= 0 ? LOGR : a.hist_log2r) : 0;
     Pair* sgrid = reinterpret_cast<Pair*>(smem_raw);
     H* shist = reinterpret_cast<H*>(sgrid + D * N);
 
@@ -621,7 +630,7 @@ __device__ __forceinline__ void iterate_body(const IterArgs& a) {
     jacobian_factors<R, D>(N, n4, nlast);
     __syncthreads();
 
-    IterateSink<R, D, ADAPT> sink(shist, N, logr);
+    IterateSink<R, D, ADAPT, ADAPT ? LOGR : -1> sink(shist, N, logr);
     bool checks_ok = sample_loop<R, D, F>(
         a.i0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x, a.i0 + a.n_chunk,
         (unsigned long long)gridDim.x * blockDim.x, it, a.integral_id << 8, a.rk0, a.rk1, a.fc,
@@ -700,11 +709,20 @@ __device__ __forceinline__ void iterate_body(const IterArgs& a) {
 // up to kBigBlockThreads per SM (float adapting iterations whose 32
 // lane-owned histogram copies fit that block's shared memory but not the
 // default budget); its own launch bound leaves the default kernels' register
-// allocation as it is.
-template <typename R, int D, int FN, bool ADAPT, bool BIG = false>
+// allocation as it is.  LOGR: the histogram copies as a compile-time 2^LOGR
+// (the float adapting kernels, whose launches use 32 copies but where they
+// fit neither shape), -1 for the count in the arguments.
+template <typename R, int D, int FN, bool ADAPT, bool BIG = false, int LOGR = -1>
 __global__ void __launch_bounds__(BIG ? kBigBlockThreads : 256)
     vegas_iterate_kernel(const IterArgs a) {
-    iterate_body<R, D, Integrand<R, FN>, ADAPT>(a);
+    iterate_body<R, D, Integrand<R, FN>, ADAPT, LOGR>(a);
+}
+
+// the copies of the default table's adapting kernel: 32 for float, the
+// run-time count for double
+template <typename R>
+constexpr int table_adapt_logr() {
+    return sizeof(R) == 4 ? 5 : -1;
 }
 
 // The same kernel for an integrand type F supplied by the caller's own
@@ -718,10 +736,12 @@ __global__ void VEGAS_ITERATE_BOUNDS vegas_user_iterate_kernel(const IterArgs a)
 
 }  // namespace vegas
 
-// Kernel table of one (precision, integrand): index [dim - 1][adapt].
+// Kernel table of one (precision, integrand): index [dim - 1][adapt].  The
+// float adapting kernels of this table run 32 histogram copies.
 #define VEGAS_KERNEL_ROW(R, FN, D) \
     {(const void*)&vegas::vegas_iterate_kernel<R, D, FN, false>, \
-     (const void*)&vegas::vegas_iterate_kernel<R, D, FN, true>}
+     (const void*)&vegas::vegas_iterate_kernel<R, D, FN, true, false, \
+                                               vegas::table_adapt_logr<R>()>}
 
 // The big-block adapting kernels of one float integrand: index [dim - 1].
 #define VEGAS_KERNEL_TABLE_BIG(name, FN)                                                     \
@@ -737,7 +757,24 @@ __global__ void VEGAS_ITERATE_BOUNDS vegas_user_iterate_kernel(const IterArgs a)
         return table[dim - 1];                                                                \
     }                                                                                         \
     }
-#define VEGAS_BIG(FN, D) (const void*)&vegas::vegas_iterate_kernel<float, D, FN, true, true>
+#define VEGAS_BIG(FN, D) (const void*)&vegas::vegas_iterate_kernel<float, D, FN, true, true, 5>
+
+// The float adapting kernels of one integrand with the run-time copy count
+// (launches whose 32 copies fit neither shape): index [dim - 1].
+#define VEGAS_KERNEL_TABLE_FEW(name, FN)                                                     \
+    namespace vegas {                                                                         \
+    const void* name(int dim) {                                                               \
+        static const void* const table[kMaxDim] = {                                           \
+            VEGAS_FEW(FN, 1),  VEGAS_FEW(FN, 2),  VEGAS_FEW(FN, 3),  VEGAS_FEW(FN, 4),          \
+            VEGAS_FEW(FN, 5),  VEGAS_FEW(FN, 6),  VEGAS_FEW(FN, 7),  VEGAS_FEW(FN, 8),          \
+            VEGAS_FEW(FN, 9),  VEGAS_FEW(FN, 10), VEGAS_FEW(FN, 11), VEGAS_FEW(FN, 12),         \
+            VEGAS_FEW(FN, 13), VEGAS_FEW(FN, 14), VEGAS_FEW(FN, 15), VEGAS_FEW(FN, 16),         \
+            VEGAS_FEW(FN, 17), VEGAS_FEW(FN, 18), VEGAS_FEW(FN, 19), VEGAS_FEW(FN, 20)};        \
+        if (dim < 1 || dim > kMaxDim) return nullptr;                                         \
+        return table[dim - 1];                                                                \
+    }                                                                                         \
+    }
+#define VEGAS_FEW(FN, D) (const void*)&vegas::vegas_iterate_kernel<float, D, FN, true, false, -1>
 
 #define VEGAS_KERNEL_TABLE(name, R, FN)                                                       \
     namespace vegas {                                                                         \

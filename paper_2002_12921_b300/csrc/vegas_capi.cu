@@ -51,6 +51,23 @@ const void* iterate_kernel_f32_big(int integrand, int dim) {
     }
 }
 
+const void* iterate_table_few_f32_gauss(int dim);
+const void* iterate_table_few_f32_mix2(int dim);
+const void* iterate_table_few_f32_flat(int dim);
+const void* iterate_table_few_f32_genz_disc(int dim);
+const void* iterate_table_few_f32_genz_ppeak(int dim);
+
+const void* iterate_kernel_f32_few(int integrand, int dim) {
+    switch (integrand) {
+    case VEGAS_GAUSS: return iterate_table_few_f32_gauss(dim);
+    case VEGAS_GAUSS_MIX2: return iterate_table_few_f32_mix2(dim);
+    case VEGAS_FLAT: return iterate_table_few_f32_flat(dim);
+    case VEGAS_GENZ_DISC: return iterate_table_few_f32_genz_disc(dim);
+    case VEGAS_GENZ_PPEAK: return iterate_table_few_f32_genz_ppeak(dim);
+    default: return nullptr;
+    }
+}
+
 const void* iterate_kernel_f64(int integrand, int dim, bool adapt) {
     switch (integrand) {
     case VEGAS_GAUSS: return iterate_table_f64_gauss(dim, adapt);
@@ -471,6 +488,11 @@ static int enqueue_iteration(vegas_state* s, uint64_t begin, uint64_t end, int a
         block = kBigBlockThreads;
         kern = iterate_kernel_f32_big(s->integrand, s->dim);
     }
+    // the float adapting kernels of the default table run 32 copies; fewer
+    // take the kernel with the run-time count
+    if (ad && !user && s->mode == VEGAS_FP32_EVAL && log2r < 5 && block != kBigBlockThreads)
+        kern = iterate_kernel_f32_few(s->integrand, s->dim);
+    if (!user && !kern) return VEGAS_EINVAL;
     const size_t smem = iterate_smem_bytes(s->mode, s->dim, s->nbins, ad, log2r);
     int occ = 0;
     if (user) {

@@ -113,6 +113,9 @@ struct RefineArgs {
 const void* iterate_kernel_f32(int integrand, int dim, bool adapt);
 // The float big-block adapting kernel (kBigBlockThreads threads per block).
 const void* iterate_kernel_f32_big(int integrand, int dim);
+// The float adapting kernel of the default shape with the run-time histogram
+// copy count (iterate_kernel_f32's adapting kernels run 32 copies).
+const void* iterate_kernel_f32_few(int integrand, int dim);
 const void* iterate_kernel_f64(int integrand, int dim, bool adapt);
 // Shared histogram copies of an adapting iterate block, as log2: 32 copies
 // (one per lane) where they fit in kHistCopyBudget bytes, fewer otherwise.
