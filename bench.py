@@ -429,9 +429,11 @@ def graph_timing(V, stream, reps=5):
 def batch_timing(V, stream, reps=5):
     """256 independent Gaussians (d ~ U{2..16}, n log-uniform in [1e4, 1e6],
     a ~ U(0.05, 0.3), centres ~ U(0.2, 0.8), 50 bins) x 8 adapting iterations:
-    autotuned tile and block size, the whole schedule captured in one CUDA
-    graph; samples/s of graph replays and of the same schedule enqueued
-    eagerly, per precision."""
+    autotuned block size (128, 256, 512), samples per thread (tile = block x
+    1 .. 512) and tile per dimension bucket, the whole schedule captured in one
+    CUDA graph; samples/s of graph replays and of the same schedule enqueued
+    eagerly, per precision (tuned_ms: the tuner's best single adapting
+    iteration)."""
     import torch
 
     from paper_2002_12921_b300 import workloads as W
@@ -445,7 +447,7 @@ def batch_timing(V, stream, reps=5):
            "products_per_run": 8 * sum(n * products_per_sample(d) for d, n in zip(dims, ns))}
     for name, mode in (("fp32", V.VEGAS_FP32_EVAL), ("fp64", V.VEGAS_FP64)):
         B = V.VegasBatch(dims, ns, 50, wls[0].seed, mode, params, max_iters=8, stream=stream)
-        choice, _ = V.binding.autotune_batch(B, reps=1)
+        choice, cands = V.binding.autotune_batch(B, reps=1)
         graph = B.capture(8)
         graph.replay()
         torch.cuda.synchronize()
@@ -467,7 +469,9 @@ def batch_timing(V, stream, reps=5):
         res[name] = {"graph_ms": times["graph"], "eager_ms": times["eager"],
                      "samples_per_s": total / (times["graph"] / 1e3),
                      "block_threads": choice[0], "tile_samples": choice[1],
-                     "tiles_by_dim": {str(d): t for d, t in sorted(choice[2].items())}}
+                     "samples_per_thread": choice[1] // choice[0],
+                     "tiles_by_dim": {str(d): t for d, t in sorted(choice[2].items())},
+                     "tuned_ms": min(cands.values()), "candidates": len(cands)}
     return res
 
 

@@ -319,14 +319,16 @@ int vegas_batch_init_integrand(vegas_batch **out, int count, const int *dims,
                                int integrand, const double *params, const double *box_lo,
                                const double *box_hi, int max_iters, void *d_workspace,
                                size_t ws_bytes, void *cuda_stream);
-/* Block size (32..256, multiple of 32) and samples per tile (>= 4096, multiple
- * of 32); 0 keeps the current value.  Rebuilds the tile table.  At the default
- * block size (256), float adapting rounds run as one 768-thread block per SM
- * when 32 histogram copies for the widest integral need it and fit. */
+/* Block size (32..512, multiple of 32) and samples per tile (>= 128, multiple
+ * of 32; a tile of block size x s gives each thread s samples); 0 keeps the
+ * current value.  Rebuilds the tile table.  At the default block size (256),
+ * float adapting rounds run as one 768-thread block per SM when 32 histogram
+ * copies for the widest integral need it and fit.  Results do not depend on
+ * either (the samples are functions of their counters). */
 int vegas_batch_set_config(vegas_batch *b, int block_threads, uint64_t tile_samples);
 /* Samples per tile by dimension: tiles[d-1] for the integrals of dimension d
  * (d = 1 .. count, count <= VEGAS_MAX_DIM; each 0 = the vegas_batch_set_config
- * size, else >= 4096 and a multiple of 32); tiles == NULL with count 0 clears
+ * size, else >= 128 and a multiple of 32); tiles == NULL with count 0 clears
  * them.  Work per sample grows with the dimension, so smaller tiles for wide
  * integrals even out the blocks' loads.  Rebuilds the tile table; results do
  * not depend on it. */

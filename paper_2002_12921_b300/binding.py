@@ -574,7 +574,9 @@ class VegasBatch:
         import torch
 
         self.dims = [int(d) for d in dims]
+        self.n_samples = [int(n) for n in n_samples]
         self.nbins, self.max_iters = nbins, max_iters
+        self.mode, self.integrand = mode, integrand
         self.ws_bytes = vegas_batch_workspace_bytes(self.dims, n_samples, nbins, max_iters)
         self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(
@@ -727,28 +729,75 @@ class TuningTable:
                f"n=1e{bucket}"
 
     def lookup(self, dim, nbins, mode, integrand, params, n, adapt=False, **tuner_kw):
-        import json
-
         k = self.key(mode, integrand, dim, nbins, n, adapt)
         if k not in self.entries:
             cfg, _ = self.tuner(dim, nbins, mode, integrand, params, n, adapt=adapt, **tuner_kw)
             self.entries[k] = {name: int(v) for name, v in cfg.items()}
-            tmp = self.path + ".tmp"
-            with open(tmp, "w") as f:
-                json.dump(self.entries, f, indent=1, sort_keys=True)
-            os.replace(tmp, self.path)
+            self._save()
         return dict(self.entries[k])
 
+    def _save(self):
+        import json
 
-def autotune_batch(batch, blocks=(128, 256), tiles=(8192, 16384, 32768, 65536, 131072), reps=2,
-                   alpha=1.5, buckets=((1, 4), (5, 8), (9, 12), (13, 16), (17, 20))):
+        tmp = self.path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(self.entries, f, indent=1, sort_keys=True)
+        os.replace(tmp, self.path)
+
+    @staticmethod
+    def batch_key(batch):
+        """A batch's key: mode, integrand, bins, integral count, the dimension
+        buckets it spans and the decade of its samples per iteration."""
+        spans = sorted({f"{lo}-{hi}" for lo, hi in DIM_BUCKETS for d in batch.dims
+                        if lo <= d <= hi})
+        total = len(str(int(sum(batch.n_samples)))) - 1
+        return (f"batch,mode={batch.mode},integrand={batch.integrand},N={batch.nbins},"
+                f"count={len(batch.dims)},buckets={'+'.join(spans)},n=1e{total}")
+
+    def lookup_batch(self, batch, tuner=None, **tuner_kw):
+        """Configure `batch` from its stored entry -- block size, batch-wide
+        tile and one tile per dimension bucket -- tuning it first (with
+        `tuner`, autotune_batch by default) if its key is new.  Returns the
+        entry."""
+        k = self.batch_key(batch)
+        if k not in self.entries:
+            (bt, ts, by_dim), _ = (tuner or autotune_batch)(batch, **tuner_kw)
+            by_bucket = {}
+            for lo, hi in DIM_BUCKETS:
+                got = {by_dim[d] for d in range(lo, hi + 1) if d in by_dim}
+                if got:
+                    by_bucket[f"{lo}-{hi}"] = int(got.pop())
+            self.entries[k] = {"block_threads": int(bt), "tile_samples": int(ts),
+                               "tiles_by_bucket": by_bucket}
+            self._save()
+        e = self.entries[k]
+        batch.config(block_threads=e["block_threads"], tile_samples=e["tile_samples"])
+        tiles = {}
+        for span, t in e["tiles_by_bucket"].items():
+            lo, hi = (int(x) for x in span.split("-"))
+            tiles.update({d: t for d in set(batch.dims) if lo <= d <= hi})
+        batch.config_tiles_by_dim(tiles)
+        batch.reset()
+        return dict(e)
+
+
+DIM_BUCKETS = ((1, 4), (5, 8), (9, 12), (13, 16), (17, 20))
+
+
+def autotune_batch(batch, blocks=(128, 256, 512),
+                   samples_per_thread=(1, 2, 4, 8, 16, 32, 64, 128, 256, 512), tiles=None,
+                   reps=2, alpha=1.5, buckets=DIM_BUCKETS):
     """Pick the launch configuration of a batch by timing one adapting
     iteration of every integral per candidate (CUDA events on the batch's
-    stream, best of `reps`): first (block_threads, tile_samples) for the whole
-    batch, then, one dimension bucket at a time, a tile size for the integrals
-    of that bucket (half or twice the batch's, kept if faster).  Leaves the
-    batch configured with the winner and reset; returns
-    ((block_threads, tile_samples, {dim: tile}), {candidate: ms})."""
+    stream, best of `reps`).  First the batch-wide (block_threads,
+    tile_samples): every block size in `blocks` with every samples-per-thread
+    count s in `samples_per_thread` (tile = block x s, at least 128 samples),
+    or with every size in `tiles` when that is given.  Then, one dimension
+    bucket at a time, a tile size for the integrals of that bucket (half or
+    twice the batch's, kept if faster).  The samples are functions of their
+    counters, so the choice changes speed, never results.  Leaves the batch
+    configured with the winner and reset; returns ((block_threads,
+    tile_samples, {dim: tile}), {candidate: ms})."""
     import torch
 
     def time_one():
@@ -766,7 +815,9 @@ def autotune_batch(batch, blocks=(128, 256), tiles=(8192, 16384, 32768, 65536, 1
     timings = {}
     batch.config_tiles_by_dim({})
     for bt in blocks:
-        for ts in tiles:
+        sizes = tiles if tiles is not None else sorted({max(128, bt * s) for s in
+                                                        samples_per_thread})
+        for ts in sizes:
             batch.config(block_threads=bt, tile_samples=ts)
             timings[(bt, ts)] = time_one()
     bt, ts = min(timings, key=timings.get)
@@ -778,7 +829,7 @@ def autotune_batch(batch, blocks=(128, 256), tiles=(8192, 16384, 32768, 65536, 1
         if not dims:
             continue
         for cand in (ts // 2, ts * 2):
-            if cand < 4096:
+            if cand < 128:
                 continue
             trial = {**by_dim, **{d: cand for d in dims}}
             batch.config_tiles_by_dim(trial)

@@ -19,7 +19,7 @@ namespace {
 
 constexpr int kPostThreads = 256;
 constexpr uint64_t kDefaultTile = 65536;
-constexpr uint64_t kMinTile = 4096;
+constexpr uint64_t kMinTile = 128;  // one sample per thread of a 128-thread block
 
 struct BatchRow {
     int b, k;  // integral, dimension
@@ -289,7 +289,7 @@ int vegas_batch_init_integrand(vegas_batch** out, int count, const int* dims,
     if (!batch_shape_ok(count, dims, n_samples, nbins, max_iters) || !d_workspace)
         return VEGAS_EINVAL;
     if (mode != VEGAS_FP64 && mode != VEGAS_FP32_EVAL) return VEGAS_EINVAL;
-    if (!batch_iterate_kernel_f64(integrand, false)) return VEGAS_EINVAL;  // built-in only
+    if (!batch_iterate_kernel_f64(integrand, false, 256)) return VEGAS_EINVAL;  // built-in only
     if ((box_lo == nullptr) != (box_hi == nullptr)) return VEGAS_EINVAL;
     size_t total_params = 0, total_dims = 0;
     for (int i = 0; i < count; ++i) {
@@ -396,7 +396,7 @@ int vegas_batch_init(vegas_batch** out, int count, const int* dims, const uint64
 
 int vegas_batch_set_config(vegas_batch* b, int block_threads, uint64_t tile_samples) {
     if (!b) return VEGAS_EINVAL;
-    if (block_threads && (block_threads < 32 || block_threads > 256 || block_threads % 32))
+    if (block_threads && (block_threads < 32 || block_threads > 512 || block_threads % 32))
         return VEGAS_EINVAL;
     if (tile_samples && (tile_samples < kMinTile || tile_samples % 32 ||
                          tile_samples > (1ull << 31)))
@@ -467,9 +467,10 @@ int vegas_batch_iterate(vegas_batch* b, int adapt, double alpha) {
     std::memcpy(a.rk0, b->rk0, sizeof(a.rk0));
     std::memcpy(a.rk1, b->rk1, sizeof(a.rk1));
 
-    const void* kern = b->mode == VEGAS_FP32_EVAL ? batch_iterate_kernel_f32(b->integrand, ad)
-                                                  : batch_iterate_kernel_f64(b->integrand, ad);
     int block = b->block_threads;
+    const void* kern = b->mode == VEGAS_FP32_EVAL
+                           ? batch_iterate_kernel_f32(b->integrand, ad, block)
+                           : batch_iterate_kernel_f64(b->integrand, ad, block);
     // float adapting rounds whose 32 copies for the widest integral miss the
     // default budget run as one big block per SM when they fit it (as the
     // single-integral kernels do), at the default block size only

@@ -97,12 +97,12 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchTile& 
     __syncthreads();  // the next tile restages the shared memory
 }
 
-// BIG: the instantiation for one block of up to kBigBlockThreads per SM (float
-// adapting rounds whose 32 histogram copies for the widest integral miss the
-// default budget but fit that block), with its own launch bound.
-template <typename R, int FN, bool ADAPT, bool BIG = false>
-__global__ void __launch_bounds__(BIG ? kBigBlockThreads : 256)
-    batch_iterate_kernel(const BatchArgs a) {
+// BOUND: the largest block the instantiation launches with (its launch
+// bound): 256 (blocks of 32..256 threads), 512 (257..512), or kBigBlockThreads
+// for one block per SM (float adapting rounds whose 32 histogram copies for the
+// widest integral miss the default budget but fit that block).
+template <typename R, int FN, bool ADAPT, int BOUND = 256>
+__global__ void __launch_bounds__(BOUND) batch_iterate_kernel(const BatchArgs a) {
     using P = Prec<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sred[32];
@@ -131,29 +131,34 @@ __global__ void __launch_bounds__(BIG ? kBigBlockThreads : 256)
     }
 }
 
-// the batch iterate kernel of a precision and built-in integrand, for the
-// host (batch_f32.cu / batch_f64.cu; nullptr for an integrand it lacks)
-const void* batch_iterate_kernel_f32(int integrand, bool adapt);
-const void* batch_iterate_kernel_f64(int integrand, bool adapt);
+// the batch iterate kernel of a precision and built-in integrand for blocks of
+// `block` threads (<= 512), for the host (batch_f32.cu / batch_f64.cu; nullptr
+// for an integrand it lacks)
+const void* batch_iterate_kernel_f32(int integrand, bool adapt, int block);
+const void* batch_iterate_kernel_f64(int integrand, bool adapt, int block);
 // the float big-block adapting kernel of an integrand (batch_f32.cu)
 const void* batch_iterate_kernel_f32_big(int integrand);
 
 }  // namespace vegas
 
-// One (precision, integrand) pair's kernels, both adapt flags, as the
-// function NAME(adapt) (one source file each, so that they compile in parallel).
-#define VEGAS_BATCH_TABLE(NAME, R, FN)                                          \
-    namespace vegas {                                                           \
-    const void* NAME(bool adapt) {                                              \
-        return adapt ? (const void*)&batch_iterate_kernel<R, FN, true>          \
-                     : (const void*)&batch_iterate_kernel<R, FN, false>;        \
-    }                                                                           \
+// One (precision, integrand) pair's kernels, both adapt flags and both launch
+// bounds, as the function NAME(adapt, block) (one source file each, so that
+// they compile in parallel).
+#define VEGAS_BATCH_TABLE(NAME, R, FN)                                                   \
+    namespace vegas {                                                                    \
+    const void* NAME(bool adapt, int block) {                                            \
+        if (block > 256)                                                                 \
+            return adapt ? (const void*)&batch_iterate_kernel<R, FN, true, 512>          \
+                         : (const void*)&batch_iterate_kernel<R, FN, false, 512>;        \
+        return adapt ? (const void*)&batch_iterate_kernel<R, FN, true>                   \
+                     : (const void*)&batch_iterate_kernel<R, FN, false>;                 \
+    }                                                                                    \
     }
 
 // The float big-block adapting kernel of one integrand, as NAME().
 #define VEGAS_BATCH_TABLE_BIG(NAME, FN)                                         \
     namespace vegas {                                                           \
     const void* NAME() {                                                        \
-        return (const void*)&batch_iterate_kernel<float, FN, true, true>;       \
+        return (const void*)&batch_iterate_kernel<float, FN, true, kBigBlockThreads>; \
     }                                                                           \
     }

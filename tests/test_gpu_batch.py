@@ -150,19 +150,51 @@ def test_graph_replay_equals_eager_run(mode):
 
 
 def test_autotuner_picks_a_candidate_and_keeps_results():
+    """The autotuner's space: block sizes 128, 256 and 512, samples per thread
+    (tile = block x s) from 1 up; whichever it picks, and any candidate forced,
+    the results are those of the default configuration (FP64, 1e-12)."""
     dims, ns, params = small_batch()
     B = V.VegasBatch(dims, ns, 30, 17, V.VEGAS_FP64, params, max_iters=4)
-    (bt, ts, by_dim), timings = V.binding.autotune_batch(B, blocks=(128, 256),
-                                                         tiles=(4096, 16384), reps=1)
-    assert (bt, ts) in timings and len(timings) >= 4
-    assert all(d in dims and t >= 4096 for d, t in by_dim.items())
+    (bt, ts, by_dim), timings = V.binding.autotune_batch(
+        B, blocks=(128, 256, 512), samples_per_thread=(1, 16, 256), reps=1)
+    assert (bt, ts) in timings and len(timings) >= 9
+    assert {(512, 512), (128, 128), (256, 65536)} <= set(timings)
+    assert all(d in dims and t >= 128 for d, t in by_dim.items())
     B.run(2)
     tuned = B.log()[:, :2, 4]
-    B.config(block_threads=256, tile_samples=4096)
-    B.config_tiles_by_dim({})
-    B.run(2)
-    assert np.allclose(B.log()[:, :2, 4], tuned, rtol=1e-12)
+    for cfg in ((256, 65536), (512, 512), (128, 128)):
+        B.config(block_threads=cfg[0], tile_samples=cfg[1])
+        B.config_tiles_by_dim({})
+        B.run(2)
+        assert np.allclose(B.log()[:, :2, 4], tuned, rtol=1e-12), cfg
     B.close()
+
+
+@pytest.mark.parametrize("mode", [V.VEGAS_FP64, V.VEGAS_FP32_EVAL])
+def test_tuning_table_configures_a_batch_without_changing_results(mode, tmp_path):
+    """TuningTable.lookup_batch tunes a batch (512-thread blocks included),
+    keeps its choice per dimension bucket and configures a second batch of
+    the same key from the file; both give the default configuration's
+    results (FP64 1e-12; FP32 the first, uniform-grid iteration to 1e-6, the
+    float histogram's atomics landing in another order afterwards)."""
+    dims, ns, params = small_batch()
+    ref = V.VegasBatch(dims, ns, 30, 23, mode, params, max_iters=3)
+    ref.run(2)
+    expect = ref.log()[:, :2, 4]
+    ref.close()
+    path = str(tmp_path / "tuning.json")
+    for _ in range(2):
+        B = V.VegasBatch(dims, ns, 30, 23, mode, params, max_iters=3)
+        e = V.binding.TuningTable(path).lookup_batch(
+            B, blocks=(256, 512), samples_per_thread=(16, 256), reps=1)
+        assert e["block_threads"] in (256, 512)
+        B.run(2)
+        got = B.log()[:, :2, 4]
+        B.close()
+        if mode == V.VEGAS_FP64:
+            assert np.allclose(got, expect, rtol=1e-12)
+        else:
+            assert np.allclose(got[:, 0], expect[:, 0], rtol=1e-6)
 
 
 def test_tiles_by_dimension_do_not_change_results():
@@ -180,7 +212,7 @@ def test_tiles_by_dimension_do_not_change_results():
     with pytest.raises(V.VegasError):
         B = V.VegasBatch(dims, ns, 30, 19, V.VEGAS_FP64, params, max_iters=4)
         try:
-            B.config_tiles_by_dim({3: 1000})  # below the 4096 minimum
+            B.config_tiles_by_dim({3: 100})  # below the 128 minimum
         finally:
             B.close()
 
