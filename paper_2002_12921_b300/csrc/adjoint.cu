@@ -51,6 +51,7 @@ struct AdjointArgs {
     FnConsts fc;
     double two_over_c2;              // 2 / c^2, for g_a = fw (2 s / c^2 - d)
     double scale[kMaxDim + 2];       // per component: 1, 2/(a c) (x d), 1/a
+    int rowoff[kMaxDim];             // k N: row offsets of the staged grid
 };
 
 // Sums of one component's values and squares.  Double: plain sums.  Float:
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(256) gauss_adjoint_kernel(const AdjointArgs a)
     AdjointSink<R, D, GRAD> sink((R)a.two_over_c2, (R)D);
     sample_loop<R, D, GaussCoords<R, D>>(
         (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x, a.n,
-        (unsigned long long)gridDim.x * blockDim.x, a.iter, 0u, a.rk0, a.rk1, a.fc, N,
+        (unsigned long long)gridDim.x * blockDim.x, a.iter, 0u, a.rk0, a.rk1, a.fc, N, a.rowoff,
         (R)(sizeof(R) == 4 ? a.fc.C32 : a.fc.C), n4, nlast, sgrid, sink);
     sink.finish();
 
@@ -259,6 +260,7 @@ extern "C" int vegas_gauss_adjoint(vegas_state* s, const double* params, int npa
     a.n = n_samples;
     a.iter = iter;
     a.nbins = s->nbins;
+    fill_row_offsets(s->nbins, a.rowoff);
     std::memcpy(a.rk0, s->rk0, sizeof(a.rk0));
     std::memcpy(a.rk1, s->rk1, sizeof(a.rk1));
 

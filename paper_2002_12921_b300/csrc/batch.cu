@@ -466,6 +466,7 @@ int vegas_batch_iterate(vegas_batch* b, int adapt, double alpha) {
     a.staged32 = b->mode == VEGAS_FP32_EVAL ? at<float2>(b, L.staged) : nullptr;
     std::memcpy(a.rk0, b->rk0, sizeof(a.rk0));
     std::memcpy(a.rk1, b->rk1, sizeof(a.rk1));
+    fill_row_offsets(b->nbins, a.rowoff);
 
     int block = b->block_threads;
     const void* kern = b->mode == VEGAS_FP32_EVAL

@@ -46,6 +46,7 @@ struct BatchArgs {
     int hist_log2r;
     const float2* staged32;  // float path: staged pairs of every row (hist layout), else null
     unsigned rk0[10], rk1[10];
+    int rowoff[kMaxDim];     // k N: row offsets of the staged grid (fill_row_offsets)
 };
 
 // One tile of integral b with compile-time dimension D and integrand FN.
@@ -75,7 +76,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchTile& 
     IterateSink<R, D, ADAPT> sink(shist, N, logr);
     bool checks_ok = sample_loop<R, D, Integrand<R, FN>>(
         t.start + threadIdx.x, t.start + t.count, blockDim.x, a.iter, t.b << 8, a.rk0, a.rk1,
-        fc, N, (R)(sizeof(R) == 4 ? fc.C32 : fc.C), n4, nlast, sgrid, sink);
+        fc, N, a.rowoff, (R)(sizeof(R) == 4 ? fc.C32 : fc.C), n4, nlast, sgrid, sink);
 #ifdef VEGAS_DEBUG_CHECKS
     checks_ok &= edges_ok(a.edges + info.edge_off, D, N);
 #endif

@@ -374,11 +374,20 @@ __device__ __forceinline__ bool sample_loop(unsigned long long first, unsigned l
                                             unsigned long long stride, unsigned it,
                                             uint32_t c2base, const unsigned (&rk0)[10],
                                             const unsigned (&rk1)[10], const FnConsts& fc,
-                                            int N, R jstart, R n4, R nlast,
+                                            int N, const int (&rowoff)[kMaxDim], R jstart,
+                                            R n4, R nlast,
                                             const typename Prec<R>::Pair* sgrid, Sink& sink) {
     using P = Prec<R>;
     using Pair = typename P::Pair;
     constexpr int DC = (D + 3) / 4;  // Philox calls per sample
+    // Row k of the staged grid starts at k N.  Where the compiler can keep the
+    // D products in registers (fixed-grid kernels up to d = 8) it does so, and
+    // that measured fastest (d=8: 743 us per 1e8 against 772 us with the
+    // offsets read from the parameters); with more dimensions, or the
+    // adapting kernels' extra registers, it recomputes them on the
+    // integer-multiply pipe, and the parameter offsets measured faster (d=16
+    // fixed 1371 -> 1330 us, d=8 adapting 121.4 -> 119.2 us per 1e7).
+    constexpr bool kRowOff = D > 8 || Sink::kNeedBins;
     // per-call constants of the shared first two Philox rounds, for the
     // current high word of the sample index
     const uint32_t t_key = it ^ rk1[0];
@@ -416,7 +425,7 @@ __device__ __forceinline__ bool sample_loop(unsigned long long first, unsigned l
                 if (k < D) {
                     const uint32_t j = __umulhi(w[t], (uint32_t)N);
                     const uint32_t l = w[t] * (uint32_t)N;
-                    const int gi = k * N + (int)j;
+                    const int gi = (kRowOff ? rowoff[k] : k * N) + (int)j;
                     const Pair g = sgrid[gi];
                     const R x = P::fma(P::unit(l), g.y, g.x);
 #ifdef VEGAS_DEBUG_CHECKS
@@ -634,7 +643,7 @@ __device__ __forceinline__ void iterate_body(const IterArgs& a) {
     bool checks_ok = sample_loop<R, D, F>(
         a.i0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x, a.i0 + a.n_chunk,
         (unsigned long long)gridDim.x * blockDim.x, it, a.integral_id << 8, a.rk0, a.rk1, a.fc,
-        N, (R)j0, n4, nlast, sgrid, sink);
+        N, a.rowoff, (R)j0, n4, nlast, sgrid, sink);
 #ifdef VEGAS_DEBUG_CHECKS
     checks_ok &= edges_ok(a.edges, D, N);
 #endif

@@ -65,6 +65,7 @@ struct NoAllocArgs {
     int log2r;          // shared histogram copies (as in the iterate kernel)
     unsigned rk0[10], rk1[10];
     FnConsts fc;
+    int rowoff[kMaxDim];  // k N: row offsets of the staged grid
 };
 
 // The iterate kernel with its scratch taken from the arguments above and its
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(256) noalloc_iterate_kernel(const NoAllocArgs 
     IterateSink<R, D, ADAPT> sink(shist, N, logr);
     sample_loop<R, D, Integrand<R, FN>>((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x,
                                         a.n, (unsigned long long)gridDim.x * blockDim.x, a.iter,
-                                        0u, a.rk0, a.rk1, a.fc, N,
+                                        0u, a.rk0, a.rk1, a.fc, N, a.rowoff,
                                         (R)(sizeof(R) == 4 ? a.fc.C32 : a.fc.C), n4, nlast, sgrid,
                                         sink);
     const Acc<R>& acc = sink.acc;
@@ -228,6 +229,7 @@ extern "C" int vegas_iterate_noalloc(double* d_edges, int dim, int nbins, uint64
     a.n = n_samples;
     a.iter = iter;
     a.nbins = nbins;
+    fill_row_offsets(nbins, a.rowoff);
 
     // what must start at zero: the ticket and, when adapting, the histogram
     if (cudaMemsetAsync(scratch + kNaCtrl, 0, kCtrlWords * sizeof(unsigned), stream) != cudaSuccess)

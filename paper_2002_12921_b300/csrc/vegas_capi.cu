@@ -528,6 +528,7 @@ static int enqueue_iteration(vegas_state* s, uint64_t begin, uint64_t end, int a
     std::memcpy(a.rk1, s->rk1, sizeof(a.rk1));
     a.fc = s->fc;
     a.staged32 = s->staged32;
+    fill_row_offsets(s->nbins, a.rowoff);
 
     for (uint64_t i0 = begin; i0 < end; i0 += chunk) {
         const uint64_t nc = (end - i0) < chunk ? (end - i0) : chunk;

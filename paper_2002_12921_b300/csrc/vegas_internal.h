@@ -97,7 +97,16 @@ struct IterArgs {
     unsigned rk0[10], rk1[10];  // Philox round keys k + r W
     FnConsts fc;
     const float2* staged32;     // float path: the grid's staged pairs (dim x N), or null
+    int rowoff[kMaxDim];        // k N: where row k of the staged grid starts
 };
+
+// k N for k < kMaxDim: the offsets of the staged grid's rows, passed to the
+// kernels in their parameters so that a bin's index is one addition of a
+// constant (k is a compile-time constant in the unrolled sample loop), not a
+// multiply on the integer-multiply pipe that Philox saturates.
+inline void fill_row_offsets(int nbins, int* rowoff) {
+    for (int k = 0; k < kMaxDim; ++k) rowoff[k] = k * nbins;
+}
 
 struct RefineArgs {
     double* edges = nullptr;  // dim x (N+1), refined in place

@@ -465,6 +465,41 @@ def test_full_size_d8_workload_one_step_parity(mode):
                                rtol=RTOL64, atol=1e-15), t
 
 
+@pytest.mark.parametrize("dim,sched", [(4, [(100_000, 1)] * 5),
+                                       (8, [(1_000_000, 1)] * 8 + [(10_000_000, 0)] * 2)])
+def test_fp64_every_step_of_a_whole_run_at_1e12(dim, sched):
+    """FP64, every iteration of a whole run (config 1, and the d=8 schedule at
+    reduced sample counts), one step at a time: the oracle recomputes
+    iteration t on the grid the GPU ran it on (I and var 1e-12, every bin of
+    the histogram 1e-11) and refines the GPU's own histogram into the GPU's
+    next grid (1e-12).  Chained over the run, this is the whole run at the FP64
+    bound; only comparing two independent runs needs the wider bound of
+    fp64_tol, because each refinement amplifies the previous steps' rounding
+    differences."""
+    p = W.gauss_params(dim, 0.1)
+    v = V.Vegas(dim, 50, 3, V.VEGAS_FP64, W.GAUSS, p, max_iters=len(sched) + 1)
+    grids, hists = [], {}
+    for t, (n, adapt) in enumerate(sched):
+        grids.append(v.grid())
+        v.iterate(n, adapt)
+        if adapt:
+            hists[t] = v.histogram()
+            v.refine(1.5)
+    grids.append(v.grid())
+    rows = v.iterations()
+    v.close()
+    for t, (n, adapt) in enumerate(sched):
+        o = oracle.iterate(grids[t], 3, t, n, W.GAUSS, p, adapt, nthreads=8)
+        assert rel(rows[t][4], o["I"]) < RTOL64, (t, rows[t][4], o["I"])
+        assert rel(rows[t][5], o["var"]) < 1e-10, t
+        if adapt:
+            assert np.allclose(hists[t], o["hist"], rtol=1e-11, atol=0), t
+            assert np.allclose(grids[t + 1], oracle.refine(grids[t], hists[t], 1.5),
+                               rtol=RTOL64, atol=1e-15), t
+        else:
+            assert np.array_equal(grids[t + 1], grids[t]), t
+
+
 def _range_sums(mode, wl, grid, t, begin, end):
     """{S1, S2, nonfinite} of samples [begin, end) of iteration t of wl on
     `grid`, from a state advanced to iteration t (vegas_iterate_range)."""
