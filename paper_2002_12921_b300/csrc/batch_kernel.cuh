@@ -50,7 +50,9 @@ struct BatchArgs {
 };
 
 // One tile of integral b with compile-time dimension D and integrand FN.
-template <typename R, int D, int FN, bool ADAPT>
+// LOGR >= 0: the tile's histogram copies as a compile-time 2^LOGR (the
+// big-block kernel always runs 32); -1: chosen per tile below.
+template <typename R, int D, int FN, bool ADAPT, int LOGR = -1>
 __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchTile& t,
                                            typename Prec<R>::Pair* sgrid,
                                            typename Prec<R>::Hist* shist, double* sred,
@@ -61,7 +63,9 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchTile& 
     // copies as fit in it, up to one per lane (lanes of a warp that share a
     // copy make the shared atomics retry).
     int logr = 0;
-    if (ADAPT) {
+    if (ADAPT && LOGR >= 0) {
+        logr = LOGR;
+    } else if (ADAPT) {
         logr = a.hist_log2r;
         while (logr < 5 && (D << (logr + 1)) <= (a.max_dim << a.hist_log2r)) ++logr;
     }
@@ -73,7 +77,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchTile& 
     jacobian_factors<R, D>(N, n4, nlast);
     __syncthreads();
 
-    IterateSink<R, D, ADAPT> sink(shist, N, logr);
+    IterateSink<R, D, ADAPT, ADAPT ? LOGR : -1> sink(shist, N, logr);
     bool checks_ok = sample_loop<R, D, Integrand<R, FN>>(
         t.start + threadIdx.x, t.start + t.count, blockDim.x, a.iter, t.b << 8, a.rk0, a.rk1,
         fc, N, a.rowoff, (R)(sizeof(R) == 4 ? fc.C32 : fc.C), n4, nlast, sgrid, sink);
@@ -120,7 +124,10 @@ __global__ void __launch_bounds__(BOUND) batch_iterate_kernel(const BatchArgs a)
         const BatchTile t = a.tiles[ti];
         switch (a.info[t.b].dim) {
 #define VEGAS_BATCH_CASE(D) \
-    case D: batch_tile<R, D, FN, ADAPT>(a, t, sgrid, shist, sred, sbad); break;
+    case D:                                                                        \
+        batch_tile<R, D, FN, ADAPT, BOUND == kBigBlockThreads ? 5 : -1>(a, t, sgrid, shist, \
+                                                                       sred, sbad);   \
+        break;
             VEGAS_BATCH_CASE(1) VEGAS_BATCH_CASE(2) VEGAS_BATCH_CASE(3) VEGAS_BATCH_CASE(4)
             VEGAS_BATCH_CASE(5) VEGAS_BATCH_CASE(6) VEGAS_BATCH_CASE(7) VEGAS_BATCH_CASE(8)
             VEGAS_BATCH_CASE(9) VEGAS_BATCH_CASE(10) VEGAS_BATCH_CASE(11) VEGAS_BATCH_CASE(12)
