@@ -41,9 +41,9 @@ EXACT = math.erf(0.5 / A) ** DIM
 SMS, LANES_PER_SM, SM_MAX_MHZ = 148, 128, 2032.0
 ALU_PEAK_TOPS = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
 
-# DRAM bytes per launch of the fixed-grid FP32 iterate kernel (read 65.3 KB,
+# DRAM bytes per launch of the fixed-grid FP32 iterate kernel (read 67.8 KB,
 # write 0 per 1e8-sample launch) from an ncu capture of this kernel build.
-ITERATE_TRAFFIC_BYTES = 65280
+ITERATE_TRAFFIC_BYTES = 67840
 
 
 def products_per_sample(d):
