@@ -673,18 +673,18 @@ def cpu_baseline(fast=False):
                         "sample": f"d=16 mixture, one {wl.chunk:.0e}-sample chunk of an "
                                   f"adapting iteration (the GPU's launch size), {cores} threads"}
         # the oracle's rate against its thread count (the paper's CPU scaling
-        # with cores, Sec. 3.3-3.4): one fixed-grid d=8 iteration of 4e6
+        # with cores, Sec. 3.3-3.4): one fixed-grid d=8 iteration of 1e7
         # samples on the uniform grid per thread count
         sweep, t = {}, 1
         e8 = oracle.uniform_grid(DIM, NBINS)
         while t <= cores:
             t0 = time.perf_counter()
-            oracle.iterate(e8, 2, 0, 4_000_000, W.GAUSS, W.gauss_params(DIM, A), False,
+            oracle.iterate(e8, 2, 0, N_ADAPT, W.GAUSS, W.gauss_params(DIM, A), False,
                            nthreads=t)
-            sweep[str(t)] = 4_000_000 / (time.perf_counter() - t0)
+            sweep[str(t)] = N_ADAPT / (time.perf_counter() - t0)
             t = t * 2 if t * 2 <= cores or t == cores else cores
         out["thread_scaling"] = {"unit": "samples/s", "samples_per_s_by_threads": sweep,
-                                 "sample": "d=8 Gaussian, one fixed-grid iteration of 4e6 "
+                                 "sample": "d=8 Gaussian, one fixed-grid iteration of 1e7 "
                                            "samples on the uniform grid per thread count"}
     return out
 

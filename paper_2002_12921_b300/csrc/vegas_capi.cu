@@ -305,7 +305,11 @@ const void* kernel_for(const vegas_state* s, bool adapt) {
 // Resident blocks per SM of `kern` launched with (block, smem) on the state's
 // device (current): on the first use of that shape the kernel's dynamic
 // shared-memory limit is raised where needed and the occupancy queried; later
-// iterations read the answer from the state.
+// iterations read the answer from the state.  The limit is a property of the
+// kernel, shared by every state that launches it, so it is raised to what a
+// block may use on this device rather than to this shape's size: a state with
+// a smaller histogram can then never lower it under another state's cached
+// shape.
 cudaError_t launch_shape(vegas_state* s, const void* kern, int block, size_t smem, int* occ) {
     for (int i = 0; i < s->n_shapes; ++i) {
         const vegas_state::LaunchShape& c = s->shapes[i];
@@ -317,7 +321,8 @@ cudaError_t launch_shape(vegas_state* s, const void* kern, int block, size_t sme
     // static shared memory (~0.5 KB) counts against the 48 KB default as well
     cudaError_t e = cudaSuccess;
     if (smem > 40 * 1024)
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem > (size_t)s->smem_optin ? (int)smem : s->smem_optin);
     int o = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, block, smem);
     if (e != cudaSuccess) return e;

@@ -60,3 +60,35 @@ def test_concurrent_states_on_their_own_streams_and_threads():
         assert np.array_equal(rows[:, 2:4], ref_rows[:, 2:4]), i
         assert np.allclose(rows[:, 4], ref_rows[:, 4], rtol=tol, atol=0), i
         assert np.allclose(grid, ref_grid, rtol=0, atol=10 * tol), i
+
+
+def test_states_sharing_a_kernel_with_different_shared_memory():
+    """Two float states of one kernel (d=8 adapting, 32 histogram copies) with
+    different bin counts need different dynamic shared memory (54.4 KB at 50
+    bins, 43.5 KB at 40); each state prepares a launch shape once and keeps
+    it.  Iterations interleaved between them run and equal each state's run
+    on its own."""
+    import paper_2002_12921_b300 as V
+    from paper_2002_12921_b300 import workloads as W
+
+    p = W.gauss_params(8, 0.1)
+    alone = []
+    for nbins in (50, 40):
+        v = V.Vegas(8, nbins, 5, V.VEGAS_FP32_EVAL, W.GAUSS, p, max_iters=4)
+        v.run([(1_000_000, 1)] * 3)
+        alone.append(v.iterations())
+        v.close()
+    a = V.Vegas(8, 50, 5, V.VEGAS_FP32_EVAL, W.GAUSS, p, max_iters=4)
+    b = V.Vegas(8, 40, 5, V.VEGAS_FP32_EVAL, W.GAUSS, p, max_iters=4)
+    for _ in range(3):
+        a.iterate(1_000_000, 1)
+        b.iterate(1_000_000, 1)
+        a.refine(1.5)
+        b.refine(1.5)
+    for v, ref in zip((a, b), alone):
+        rows = v.iterations()
+        v.close()
+        assert np.array_equal(rows[:, 2], ref[:, 2])
+        # the first iteration is on the uniform grid: the same sums to float order
+        assert np.allclose(rows[0, 4], ref[0, 4], rtol=1e-6)
+        assert np.allclose(rows[:, 4], ref[:, 4], rtol=1e-4)
