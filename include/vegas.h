@@ -168,12 +168,17 @@ int vegas_set_box(vegas_state *s, const double *lo, const double *hi);
 /* Change the launch configuration (cfg == NULL restores the defaults). */
 int vegas_set_config(vegas_state *s, const vegas_config *cfg);
 
-/* Run one iteration of n_samples >= 2 samples on the current grid (the
- * per-event step of Sec. 2.2).  adapt != 0 also adds each sample's (fJ)^2 to
+/* Run one iteration of n_samples >= 2 samples (at most VEGAS_MAX_SAMPLE_INDEX)
+ * on the current grid (the per-event step of Sec. 2.2).  adapt != 0 also adds each sample's (fJ)^2 to
  * the histogram bin of each dimension for the next vegas_refine.  Appends
  * (S1, S2, n, nonfinite, I = S1/n, var = (S2/n - I^2)/(n-1)) to the device log.
  * Asynchronous; VEGAS_ESTATE if the log is full. */
 int vegas_iterate(vegas_state *s, uint64_t n_samples, int adapt);
+
+/* Sample indices stay below this bound (2^64 - 2^33) in every call that takes
+ * them (n_samples, n_total, i0 + n): a thread's next index then never wraps
+ * around 2^64.  Larger values return VEGAS_EINVAL. */
+#define VEGAS_MAX_SAMPLE_INDEX 0xFFFFFFFE00000000ull
 
 /* Refine the grid from the accumulated histogram and clear it (the
  * after-iteration step of Sec. 2.2; Lepage 1978 Sec. 3 and the 1980 report):
@@ -228,8 +233,8 @@ int vegas_get_histogram(vegas_state *s, double *host_hist);
 /* Write the Philox4x32-10 words that samples i0 .. i0+n-1 of iteration iter
  * draw (the counter layout above) to d_out, n x dim uint32 rows in device
  * memory owned by the caller; the same device function the iterate kernel
- * uses.  A reproducibility and test aid.  dim in [1, 20]; asynchronous on the
- * stream. */
+ * uses.  A reproducibility and test aid.  dim in [1, 20], n at most
+ * VEGAS_MAX_SAMPLE_INDEX; asynchronous on the stream. */
 int vegas_sample_words(uint64_t seed, uint32_t integral_id, uint32_t iter, uint64_t i0,
                        uint64_t n, int dim, uint32_t *d_out, void *cuda_stream);
 
@@ -247,7 +252,7 @@ int vegas_sample_words(uint64_t seed, uint32_t integral_id, uint32_t iter, uint6
  * 3 + dim*nbins doubles: {S1, S2, nonfinite, histogram (dim x nbins)}. */
 
 /* Samples [i_begin, i_end) of an iteration of n_total samples (0 <= i_begin <
- * i_end <= n_total).  The log row holds this range's sums until
+ * i_end <= n_total <= VEGAS_MAX_SAMPLE_INDEX).  The log row holds this range's sums until
  * vegas_shard_import replaces them.  Asynchronous. */
 int vegas_iterate_range(vegas_state *s, uint64_t n_total, uint64_t i_begin, uint64_t i_end,
                         int adapt);

@@ -40,7 +40,8 @@ __global__ void sample_words_kernel(const WordsArgs a) {
 extern "C" int vegas_sample_words(uint64_t seed, uint32_t integral_id, uint32_t iter, uint64_t i0,
                                   uint64_t n, int dim, uint32_t* d_out, void* cuda_stream) {
     using namespace vegas;
-    if (dim < 1 || dim > kMaxDim || (n > 0 && !d_out)) return VEGAS_EINVAL;
+    if (dim < 1 || dim > kMaxDim || (n > 0 && !d_out) || n > VEGAS_MAX_SAMPLE_INDEX)
+        return VEGAS_EINVAL;
     if (n == 0) return VEGAS_OK;
     WordsArgs a;
     a.i0 = i0;

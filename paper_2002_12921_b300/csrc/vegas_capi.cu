@@ -603,13 +603,15 @@ int vegas_set_user_integrand(vegas_state* s, const vegas_user_integrand* u, cons
 }
 
 int vegas_iterate(vegas_state* s, uint64_t n_samples, int adapt) {
-    if (!s || n_samples < 2) return VEGAS_EINVAL;
+    if (!s || n_samples < 2 || n_samples > VEGAS_MAX_SAMPLE_INDEX) return VEGAS_EINVAL;
     return enqueue_iteration(s, 0, n_samples, adapt);
 }
 
 int vegas_iterate_range(vegas_state* s, uint64_t n_total, uint64_t i_begin, uint64_t i_end,
                         int adapt) {
-    if (!s || n_total < 2 || i_begin >= i_end || i_end > n_total) return VEGAS_EINVAL;
+    if (!s || n_total < 2 || n_total > VEGAS_MAX_SAMPLE_INDEX || i_begin >= i_end ||
+        i_end > n_total)
+        return VEGAS_EINVAL;
     return enqueue_iteration(s, i_begin, i_end, adapt);
 }
 

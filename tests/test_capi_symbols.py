@@ -107,3 +107,13 @@ def test_fp64_exp_table_is_correctly_rounded_powers_of_two():
     for j, v in enumerate(vals):
         exact = mpmath.mpf(2) ** (mpmath.mpf(j) / 64)
         assert abs(mpmath.mpf(v) - exact) <= mpmath.mpf(np.spacing(v)) / 2, j
+
+
+def test_sample_words_refuses_counts_beyond_the_index_bound(lib):
+    """vegas_sample_words checks n against VEGAS_MAX_SAMPLE_INDEX before any
+    device work (the pointer is never touched)."""
+    import ctypes
+
+    rc = lib.vegas_sample_words(1, 0, 0, 0, V.binding.VEGAS_MAX_SAMPLE_INDEX + 1, 4,
+                                ctypes.c_void_p(0x1000), None)
+    assert rc == V.VEGAS_EINVAL

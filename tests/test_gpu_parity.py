@@ -519,6 +519,48 @@ def _range_sums(mode, wl, grid, t, begin, end):
 
 
 @pytest.mark.parametrize("mode", [V.VEGAS_FP64, V.VEGAS_FP32_EVAL])
+@pytest.mark.parametrize("dim,adapt", [(8, False), (3, False), (8, True)])
+@pytest.mark.parametrize("first", [2**32 - 1_000_000, V.VEGAS_MAX_SAMPLE_INDEX - 2**32 - 1_000_000,
+                                   V.VEGAS_MAX_SAMPLE_INDEX - 2_000_000])
+def test_sample_ranges_across_a_high_word_boundary(mode, dim, adapt, first):
+    """Index ranges whose threads cross a multiple of 2^32 (where the sample
+    loop starts a new run of one high word and recomputes the per-call Philox
+    constants), the last such crossing below the index bound, and the range
+    that ends at the bound: the fixed-grid kernels above d = 4 (runs counted
+    in 32 bits), at d = 3 and adapting (the 64-bit loop).  The range's sums,
+    and in FP64 its histogram, equal the oracle's over the same indices."""
+    from paper_2002_12921_b300.shard import GpuShardEngine
+
+    p = W.gauss_params(dim, 0.1, np.linspace(0.3, 0.7, dim))
+    e = oracle.run(dim, 40, 99, W.GAUSS, p, [(100_000, 1)] * 3)["edges"]
+    count, n_total = 2_000_000, first + 2_000_000
+    v = V.Vegas(dim, 40, 6, mode, W.GAUSS, p, max_iters=2)
+    v.set_grid(e)
+    eng = GpuShardEngine(v)
+    eng.iterate_range(n_total, first, first + count, adapt)
+    got = eng.export().cpu().numpy().copy()
+    v.close()
+    o = oracle.iterate_range(e, 6, 0, first, count, W.GAUSS, p, adapt, nthreads=8)
+    tol = RTOL64 if mode == V.VEGAS_FP64 else 1e-5
+    assert got[2] == o["nonfinite"] == 0
+    assert rel(got[0], o["S1"]) < tol, (got[0], o["S1"])
+    assert rel(got[1], o["S2"]) < 2 * tol, (got[1], o["S2"])
+    if adapt and mode == V.VEGAS_FP64:
+        assert np.allclose(got[3:].reshape(dim, 40), o["hist"], rtol=1e-11, atol=0)
+
+
+def test_sample_indices_beyond_the_bound_are_refused():
+    """n_total above VEGAS_MAX_SAMPLE_INDEX (where a thread's next index could
+    wrap around 2^64) is refused before anything is enqueued."""
+    v = V.Vegas(3, 10, 1, V.VEGAS_FP32_EVAL, W.GAUSS, W.gauss_params(3, 0.1), max_iters=2)
+    top = V.VEGAS_MAX_SAMPLE_INDEX
+    assert V.lib().vegas_iterate_range(v.handle, top + 1, top - 10, top, 0) == V.VEGAS_EINVAL
+    assert V.lib().vegas_iterate(v.handle, top + 1, 0) == V.VEGAS_EINVAL
+    assert V.lib().vegas_iterate_range(v.handle, top, top - 10, top, 0) == V.VEGAS_OK
+    v.close()
+
+
+@pytest.mark.parametrize("mode", [V.VEGAS_FP64, V.VEGAS_FP32_EVAL])
 def test_full_size_d16_mixture_sampled_parity(mode):
     """The d=16 mixture at full size (iterations of 1e9 samples in 1e8-sample
     launches, as bench.py runs it): on the grid of the third iteration, two
