@@ -234,7 +234,8 @@ int vegas_get_histogram(vegas_state *s, double *host_hist);
  * draw (the counter layout above) to d_out, n x dim uint32 rows in device
  * memory owned by the caller; the same device function the iterate kernel
  * uses.  A reproducibility and test aid.  dim in [1, 20], n at most
- * VEGAS_MAX_SAMPLE_INDEX; asynchronous on the stream. */
+ * VEGAS_MAX_SAMPLE_INDEX, d_out device memory (else VEGAS_EINVAL);
+ * asynchronous on the stream. */
 int vegas_sample_words(uint64_t seed, uint32_t integral_id, uint32_t iter, uint64_t i0,
                        uint64_t n, int dim, uint32_t *d_out, void *cuda_stream);
 
@@ -257,7 +258,11 @@ int vegas_sample_words(uint64_t seed, uint32_t integral_id, uint32_t iter, uint6
 int vegas_iterate_range(vegas_state *s, uint64_t n_total, uint64_t i_begin, uint64_t i_end,
                         int adapt);
 /* Copy the last iteration's {S1, S2, nonfinite} and the histogram into d_buf
- * (device, 3 + dim*nbins doubles).  Asynchronous. */
+ * (device, 3 + dim*nbins doubles).  Asynchronous.  Here and in
+ * vegas_shard_import, vegas_gauss_adjoint and vegas_grid_digest, the
+ * caller's buffer must be device memory on the state's device (cudaMalloc or
+ * a framework's device allocation): anything else returns VEGAS_EINVAL before
+ * anything is enqueued. */
 int vegas_shard_export(vegas_state *s, double *d_buf);
 /* Replace the last iteration's sums and the histogram by d_buf's totals and
  * recompute its I and var for n_total samples.  Asynchronous. */

@@ -236,7 +236,8 @@ extern "C" int vegas_gauss_adjoint(vegas_state* s, const double* params, int npa
                                    double* d_out) {
     vegas::TraceRange trace_("vegas_gauss_adjoint");
     using namespace vegas;
-    if (!s || !params || !d_out || nparams < 1 + s->dim) return VEGAS_EINVAL;
+    if (!s || !params || nparams < 1 + s->dim || !device_memory_on(d_out, s->device))
+        return VEGAS_EINVAL;
     if (n_samples < 2 || n_samples > (1ull << 40)) return VEGAS_EINVAL;
     AdjointArgs a;
     std::memset(&a, 0, sizeof(a));

@@ -43,6 +43,7 @@ extern "C" int vegas_sample_words(uint64_t seed, uint32_t integral_id, uint32_t 
     if (dim < 1 || dim > kMaxDim || (n > 0 && !d_out) || n > VEGAS_MAX_SAMPLE_INDEX)
         return VEGAS_EINVAL;
     if (n == 0) return VEGAS_OK;
+    if (!device_memory_on(d_out, -1)) return VEGAS_EINVAL;
     WordsArgs a;
     a.i0 = i0;
     a.n = n;

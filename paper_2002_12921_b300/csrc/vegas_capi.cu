@@ -616,7 +616,7 @@ int vegas_iterate_range(vegas_state* s, uint64_t n_total, uint64_t i_begin, uint
 }
 
 int vegas_shard_export(vegas_state* s, double* d_buf) {
-    if (!s || !d_buf) return VEGAS_EINVAL;
+    if (!s || !device_memory_on(d_buf, s->device)) return VEGAS_EINVAL;
     if (s->host_iters < 1) return VEGAS_ESTATE;
     DeviceGuard g(s->device);
     if (!g.ok) return VEGAS_ECUDA;
@@ -633,7 +633,9 @@ int vegas_shard_export(vegas_state* s, double* d_buf) {
 }
 
 int vegas_shard_import(vegas_state* s, const double* d_buf, uint64_t n_total) {
-    if (!s || !d_buf || n_total < 2) return VEGAS_EINVAL;
+    if (!s || n_total < 2 || n_total > VEGAS_MAX_SAMPLE_INDEX ||
+        !device_memory_on(d_buf, s->device))
+        return VEGAS_EINVAL;
     if (s->host_iters < 1) return VEGAS_ESTATE;
     DeviceGuard g(s->device);
     if (!g.ok) return VEGAS_ECUDA;
@@ -645,7 +647,8 @@ int vegas_shard_import(vegas_state* s, const double* d_buf, uint64_t n_total) {
 }
 
 int vegas_grid_digest(vegas_state* s, uint64_t* d_out) {
-    if (!s || !d_out || (reinterpret_cast<uintptr_t>(d_out) % 8) != 0) return VEGAS_EINVAL;
+    if (!s || (reinterpret_cast<uintptr_t>(d_out) % 8) != 0 || !device_memory_on(d_out, s->device))
+        return VEGAS_EINVAL;
     DeviceGuard g(s->device);
     if (!g.ok) return VEGAS_ECUDA;
     return cuda_status(launch_grid_digest(s->edges, s->dim * (s->nbins + 1),

@@ -204,6 +204,19 @@ inline bool injected_failure(vegas_state* s) {
     return s->inject_countdown > 0 && --s->inject_countdown == 0;
 }
 
+// Whether p is device memory of `device` (-1: of any device), the only kind a
+// kernel may be handed; a host pointer would fault the kernel, or, where the
+// GPU can reach host memory, be used silently.  Clears the error a failed
+// query leaves.
+inline bool device_memory_on(const void* p, int device) {
+    cudaPointerAttributes attr;
+    if (!p || cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice && (device < 0 || attr.device == device);
+}
+
 // Rewrite a float-path state's staged pairs after its edges changed other than
 // by vegas_refine (enqueued on the state's stream; VEGAS_OK for FP64 states).
 int restage(vegas_state* s);

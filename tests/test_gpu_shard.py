@@ -114,3 +114,27 @@ def test_grid_digest_on_the_device_equals_its_host_definition(mode):
     VirtualRanks([GpuShardEngine(s) for s in states]).run(SCHED)  # digests checked inside
     for s in states:
         s.close()
+
+
+def test_host_buffers_are_refused_where_device_memory_is_required():
+    """A host buffer handed to the calls whose kernels write or read the
+    caller's memory is refused with VEGAS_EINVAL before anything is enqueued."""
+    import ctypes
+
+    v = V.Vegas(3, 10, 1, V.VEGAS_FP64, W.GAUSS, W.gauss_params(3, 0.1), max_iters=2)
+    v.iterate(10_000, 1)
+    host = np.zeros(64)
+    hp = ctypes.c_void_p(host.ctypes.data)
+    L = V.lib()
+    assert L.vegas_shard_export(v.handle, hp) == V.VEGAS_EINVAL
+    assert L.vegas_shard_import(v.handle, hp, 10_000) == V.VEGAS_EINVAL
+    assert L.vegas_grid_digest(v.handle, hp) == V.VEGAS_EINVAL
+    p = (ctypes.c_double * 4)(*W.gauss_params(3, 0.1))
+    assert L.vegas_gauss_adjoint(v.handle, p, 4, 0, 10_000, 1, hp) == V.VEGAS_EINVAL
+    assert L.vegas_sample_words(1, 0, 0, 0, 8, 3, hp,
+                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) \
+        == V.VEGAS_EINVAL
+    torch.cuda.synchronize()
+    assert np.all(host == 0.0)
+    assert v.iterations().shape[0] == 1
+    v.close()
