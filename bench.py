@@ -41,9 +41,10 @@ EXACT = math.erf(0.5 / A) ** DIM
 SMS, LANES_PER_SM, SM_MAX_MHZ = 148, 128, 2032.0
 ALU_PEAK_TOPS = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
 
-# DRAM bytes per launch of the fixed-grid FP32 iterate kernel (read 67.8 KB,
-# write 0 per 1e8-sample launch) from an ncu capture of this kernel build.
-ITERATE_TRAFFIC_BYTES = 67840
+# DRAM bytes per launch of the fixed-grid FP32 iterate kernel (read 71.2 KB,
+# write 0 per 1e8-sample launch; the kernel compiled for 50 bins) from an ncu
+# capture of this kernel build.
+ITERATE_TRAFFIC_BYTES = 71168
 
 
 def products_per_sample(d):
@@ -71,7 +72,7 @@ def pipe_fractions(V, fixed_ms, adapt_ms):
                             "sm_mhz": v["sm_mhz"]} for k, v in peaks.items()},
            "basis": "vegas_pipe_peak: 8 independent chains per thread, every SM filled, "
                     "CUDA-event time of one launch, best of 3",
-           "fixed_kernel": {"kernel": "vegas_iterate_kernel<float,8,GAUSS,fixed>",
+           "fixed_kernel": {"kernel": "vegas_iterate_kernel<float,8,GAUSS,fixed,N=50>",
                             "samples_per_s": fixed_rate,
                             "product": frac("product", products_per_sample(DIM), fixed_rate),
                             "ex2": frac("ex2", 1, fixed_rate)}}
@@ -820,7 +821,7 @@ def main():
                 "frac_issue": achieved / ALU_PEAK_TOPS,
                 "frac_issue_kernel_count": kernel_achieved / ALU_PEAK_TOPS,
                 "traffic": ITERATE_TRAFFIC_BYTES,
-                "kernel": "vegas_iterate_kernel<float,8,GAUSS,fixed>",
+                "kernel": "vegas_iterate_kernel<float,8,GAUSS,fixed,N=50>",
                 "kernel_ms": fixed_ms, "ops_per_sample": alg_ops_per_sample(DIM),
                 "ops_per_sample_kernel_count": kernel_ops_per_sample(DIM),
                 "ops_basis": "the method's steps per sample, Philox round-key additions "

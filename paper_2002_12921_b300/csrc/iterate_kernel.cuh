@@ -625,7 +625,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // The kernel body.  R = float or double, D = dimension, F = integrand type,
 // ADAPT = accumulate the refinement histogram.
 // ------------------------------------------------------------------------
-template <typename R, int D, typename F, bool ADAPT, int LOGR = -1>
+// NB > 0: the bin count as a compile-time constant (it must equal a.nbins).
+template <typename R, int D, typename F, bool ADAPT, int LOGR = -1, int NB = 0>
 __device__ __forceinline__ void iterate_body(const IterArgs& a) {
     using P = Prec<R>;
     using Pair = typename P::Pair;
@@ -636,7 +637,7 @@ __device__ __forceinline__ void iterate_body(const IterArgs& a) {
     __shared__ unsigned sbad[32];
     __shared__ int s_last;
 
-    const int N = a.nbins;
+    const int N = NB > 0 ? NB : a.nbins;
     const int logr = ADAPT ? (LOGR >= 0 ? LOGR : a.hist_log2r) : 0;
     Pair* sgrid = reinterpret_cast<Pair*>(smem_raw);
     H* shist = reinterpret_cast<H*>(sgrid + D * N);
@@ -750,10 +751,10 @@ __device__ __forceinline__ void iterate_body(const IterArgs& a) {
 // allocation as it is.  LOGR: the histogram copies as a compile-time 2^LOGR
 // (the float adapting kernels, whose launches use 32 copies but where they
 // fit neither shape), -1 for the count in the arguments.
-template <typename R, int D, int FN, bool ADAPT, bool BIG = false, int LOGR = -1>
+template <typename R, int D, int FN, bool ADAPT, bool BIG = false, int LOGR = -1, int NB = 0>
 __global__ void __launch_bounds__(BIG ? kBigBlockThreads : 256)
     vegas_iterate_kernel(const IterArgs a) {
-    iterate_body<R, D, Integrand<R, FN>, ADAPT, LOGR>(a);
+    iterate_body<R, D, Integrand<R, FN>, ADAPT, LOGR, NB>(a);
 }
 
 // the copies of the default table's adapting kernel: 32 for float, the
@@ -813,6 +814,21 @@ __global__ void VEGAS_ITERATE_BOUNDS vegas_user_iterate_kernel(const IterArgs a)
     }                                                                                         \
     }
 #define VEGAS_FEW(FN, D) (const void*)&vegas::vegas_iterate_kernel<float, D, FN, true, false, -1>
+
+// The float fixed-grid kernels of one integrand for kFixedBins bins per
+// dimension, dimensions 1..kFixedBinsMaxDim: index [dim - 1].
+#define VEGAS_KERNEL_TABLE_NB(name, FN)                                                      \
+    namespace vegas {                                                                         \
+    const void* name(int dim) {                                                               \
+        static const void* const table[kFixedBinsMaxDim] = {                                  \
+            VEGAS_NB(FN, 1), VEGAS_NB(FN, 2), VEGAS_NB(FN, 3), VEGAS_NB(FN, 4),                \
+            VEGAS_NB(FN, 5), VEGAS_NB(FN, 6), VEGAS_NB(FN, 7), VEGAS_NB(FN, 8)};               \
+        if (dim < 1 || dim > kFixedBinsMaxDim) return nullptr;                                \
+        return table[dim - 1];                                                                \
+    }                                                                                         \
+    }
+#define VEGAS_NB(FN, D) \
+    (const void*)&vegas::vegas_iterate_kernel<float, D, FN, false, false, -1, vegas::kFixedBins>
 
 #define VEGAS_KERNEL_TABLE(name, R, FN)                                                       \
     namespace vegas {                                                                         \

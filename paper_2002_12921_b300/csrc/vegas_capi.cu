@@ -68,6 +68,23 @@ const void* iterate_kernel_f32_few(int integrand, int dim) {
     }
 }
 
+const void* iterate_table_nb_f32_gauss(int dim);
+const void* iterate_table_nb_f32_mix2(int dim);
+const void* iterate_table_nb_f32_flat(int dim);
+const void* iterate_table_nb_f32_genz_disc(int dim);
+const void* iterate_table_nb_f32_genz_ppeak(int dim);
+
+const void* iterate_kernel_f32_nb(int integrand, int dim) {
+    switch (integrand) {
+    case VEGAS_GAUSS: return iterate_table_nb_f32_gauss(dim);
+    case VEGAS_GAUSS_MIX2: return iterate_table_nb_f32_mix2(dim);
+    case VEGAS_FLAT: return iterate_table_nb_f32_flat(dim);
+    case VEGAS_GENZ_DISC: return iterate_table_nb_f32_genz_disc(dim);
+    case VEGAS_GENZ_PPEAK: return iterate_table_nb_f32_genz_ppeak(dim);
+    default: return nullptr;
+    }
+}
+
 const void* iterate_kernel_f64(int integrand, int dim, bool adapt) {
     switch (integrand) {
     case VEGAS_GAUSS: return iterate_table_f64_gauss(dim, adapt);
@@ -480,13 +497,13 @@ static int enqueue_iteration(vegas_state* s, uint64_t begin, uint64_t end, int a
     if (!user && !kern) return VEGAS_EINVAL;
     int log2r = ad ? hist_log2r(s->mode, s->dim, s->nbins) : 0;
     int block = s->cfg.block_threads;
+    const bool default_cfg = s->cfg.block_threads == 256 && s->cfg.blocks_per_sm == 0;
     // A float adapting iteration whose 32 lane-owned histogram copies miss the
     // default budget runs as one big block per SM when they fit its shared
     // memory: no two lanes of a warp then share a copy (no retried
     // compare-and-swap adds, no bank conflicts) at the same occupancy.  Only
     // under the default launch configuration.
-    if (ad && !user && s->mode == VEGAS_FP32_EVAL && log2r < 5 && s->cfg.block_threads == 256 &&
-        s->cfg.blocks_per_sm == 0 &&
+    if (ad && !user && s->mode == VEGAS_FP32_EVAL && log2r < 5 && default_cfg &&
         iterate_smem_bytes(s->mode, s->dim, s->nbins, true, 5) <= (size_t)s->smem_optin &&
         iterate_kernel_f32_big(s->integrand, s->dim)) {
         log2r = 5;
@@ -497,6 +514,11 @@ static int enqueue_iteration(vegas_state* s, uint64_t begin, uint64_t end, int a
     // take the kernel with the run-time count
     if (ad && !user && s->mode == VEGAS_FP32_EVAL && log2r < 5 && block != kBigBlockThreads)
         kern = iterate_kernel_f32_few(s->integrand, s->dim);
+    // fixed-grid float iterations at the compiled bin count (under the default
+    // launch configuration)
+    if (!ad && !user && s->mode == VEGAS_FP32_EVAL && default_cfg && s->nbins == kFixedBins &&
+        iterate_kernel_f32_nb(s->integrand, s->dim))
+        kern = iterate_kernel_f32_nb(s->integrand, s->dim);
     if (!user && !kern) return VEGAS_EINVAL;
     const size_t smem = iterate_smem_bytes(s->mode, s->dim, s->nbins, ad, log2r);
     int occ = 0;

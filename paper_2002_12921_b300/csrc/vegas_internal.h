@@ -125,6 +125,14 @@ const void* iterate_kernel_f32_big(int integrand, int dim);
 // The float adapting kernel of the default shape with the run-time histogram
 // copy count (iterate_kernel_f32's adapting kernels run 32 copies).
 const void* iterate_kernel_f32_few(int integrand, int dim);
+// The float fixed-grid kernels compiled for kFixedBins bins per dimension (the
+// bin count of the paper's workloads here; measured at d = 8: 715 -> 682 us
+// per 1e8 samples, with the bin count a constant of the index arithmetic),
+// for dimensions up to kFixedBinsMaxDim, where that measured faster (above d
+// = 8, and in the adapting kernels, it measured slower).  nullptr otherwise.
+constexpr int kFixedBins = 50;
+constexpr int kFixedBinsMaxDim = 8;
+const void* iterate_kernel_f32_nb(int integrand, int dim);
 const void* iterate_kernel_f64(int integrand, int dim, bool adapt);
 // Shared histogram copies of an adapting iterate block, as log2: 32 copies
 // (one per lane) where they fit in kHistCopyBudget bytes, fewer otherwise.

@@ -781,3 +781,34 @@ def test_pulls_over_seeds_are_standard_normal(mode):
     pulls = np.array(pulls)
     assert abs(pulls.mean()) < 3 / np.sqrt(200)
     assert abs(pulls.std() - 1) < 3 / np.sqrt(2 * 200)
+
+
+@pytest.mark.parametrize("fid,dim", [(W.GAUSS, 8), (W.GAUSS, 3), (W.GENZ_PPEAK, 6),
+                                     (W.GAUSS_MIX2, 5)])
+def test_fixed_grid_kernel_compiled_for_50_bins_equals_the_general_one(fid, dim):
+    """Float fixed-grid iterations at 50 bins (up to d = 8) run, under the
+    default launch configuration, a kernel with the bin count compiled in; the
+    general kernel (taken under an explicit blocks-per-SM setting) gives the
+    same sums up to their order of summation, and both equal the oracle's
+    within the float budget."""
+    if fid == W.GAUSS:
+        p = W.gauss_params(dim, 0.1)
+    elif fid == W.GAUSS_MIX2:
+        p = W.mix2_params(dim, 0.15)
+    else:
+        p = W.genz_params(dim, seed=dim, kind=fid)
+    e = oracle.run(dim, 50, 9, fid, p, [(100_000, 1)] * 3)["edges"]
+    rows = []
+    for cfg in ({}, {"blocks_per_sm": 4}):
+        v = V.Vegas(dim, 50, 9, V.VEGAS_FP32_EVAL, fid, p, max_iters=2)
+        v.set_grid(e)
+        if cfg:
+            v.config(**cfg)
+        v.iterate(20_000_000, 0)
+        rows.append(v.iterations()[0])
+        v.close()
+    o = oracle.iterate(e, 9, 0, 20_000_000, fid, p, False, nthreads=8)
+    for r in rows:
+        assert r[2] == 20_000_000 and r[3] == o["nonfinite"] == 0
+        assert rel(r[4], o["I"]) < 1e-5, (r[4], o["I"])
+    assert rel(rows[0][0], rows[1][0]) < 1e-7 and rel(rows[0][1], rows[1][1]) < 1e-7
