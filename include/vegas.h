@@ -147,9 +147,11 @@ int vegas_workspace_bytes(int dim, int nbins, int max_iters, size_t *bytes);
  *   d_workspace, ws_bytes  device buffer owned by the caller; it must outlive
  *              the state and must not be used by anything else meanwhile
  *   cuda_stream  the stream all work of this state is ordered on
- * On success *out receives the descriptor, which owns a small pinned host
- * buffer (cudaHostAlloc: the control words and up to 4096 log rows) through
- * which every later read of the log goes; VEGAS_ECUDA if it cannot be had.
+ * On success *out receives the descriptor, which holds a small pinned host
+ * buffer (the control words and up to 4096 log rows) through which every
+ * later read of the log goes: taken from the library's process-wide pool of
+ * page-locked blocks that destroyed states returned, else allocated with
+ * cudaHostAlloc; VEGAS_ECUDA if it cannot be had.  Thread-safe.
  * Asynchronous: the workspace is initialised by work enqueued on the stream. */
 int vegas_init_grid(vegas_state **out, int dim, int nbins, uint64_t seed, int mode, int integrand,
                     const double *params, int nparams, int max_iters, void *d_workspace,
@@ -510,8 +512,9 @@ int vegas_pipe_peak(int op, uint32_t iters, void *d_scratch, size_t scratch_byte
  * countdown 0 cancels.  Host-side only.  VEGAS_EINVAL for countdown < 0. */
 int vegas_inject_failure(vegas_state *s, int countdown);
 
-/* Release the descriptor and its pinned host staging (not the caller's
- * workspace).  Synchronises the stream first.  NULL is accepted. */
+/* Release the descriptor (not the caller's workspace); its pinned host
+ * staging goes back to the library's pool (at most 64 blocks wait there; the
+ * rest are freed).  Synchronises the stream first.  NULL is accepted. */
 int vegas_destroy(vegas_state *s);
 
 /* Static text for a status code. */

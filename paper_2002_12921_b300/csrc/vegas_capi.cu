@@ -4,7 +4,9 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -270,6 +272,68 @@ static_assert(kCtrlWords * sizeof(unsigned) <= kPinnedCtrlBytes, "control words 
 
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
+// Log rows a state's pinned staging holds: max_iters rounded up to a power of
+// two from 32, at most kPinnedLogRows, so that states of similar log lengths
+// share a block size in the pool below.
+int pinned_rows(int max_iters) {
+    int r = 32;
+    while (r < max_iters && r < kPinnedLogRows) r <<= 1;
+    return r;
+}
+
+// Process-wide pool of pinned staging blocks.  Page-locking host memory costs
+// the driver hundreds of microseconds per state and freeing it waits for the
+// device, so vegas_destroy returns a state's block here and the next state
+// that needs a block of the same size takes it; at most kPinnedPoolBlocks
+// blocks wait in the pool (the rest are freed).  Every block is allocated
+// portable, so any device's state may take it.
+constexpr size_t kPinnedPoolBlocks = 64;
+struct PinnedPool {
+    std::mutex mu;
+    std::vector<std::pair<void*, size_t>> free;  // (block, bytes)
+};
+// never destroyed: states may be released from other threads' exit paths
+PinnedPool& pinned_pool() {
+    static PinnedPool* pool = new PinnedPool;
+    return *pool;
+}
+
+void* pinned_take(size_t bytes) {
+    PinnedPool& pool = pinned_pool();
+    {
+        std::lock_guard<std::mutex> lock(pool.mu);
+        for (size_t i = 0; i < pool.free.size(); ++i) {
+            if (pool.free[i].second == bytes) {
+                void* p = pool.free[i].first;
+                pool.free[i] = pool.free.back();
+                pool.free.pop_back();
+                return p;
+            }
+        }
+    }
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, bytes, cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+// Returns the block to the pool (or frees it when the pool is full).  The
+// caller has synchronised every copy that used it.
+bool pinned_give(void* p, size_t bytes) {
+    if (!p) return true;
+    PinnedPool& pool = pinned_pool();
+    {
+        std::lock_guard<std::mutex> lock(pool.mu);
+        if (pool.free.size() < kPinnedPoolBlocks) {
+            pool.free.emplace_back(p, bytes);
+            return true;
+        }
+    }
+    return cudaFreeHost(p) == cudaSuccess;
+}
+
 struct Layout {
     size_t edges, hist, log, partials, ctrl, staged, total;
 };
@@ -319,10 +383,27 @@ const void* kernel_for(const vegas_state* s, bool adapt) {
                                       : iterate_kernel_f64(s->integrand, s->dim, adapt);
 }
 
+// Launch shapes prepared by any state, with their device: a state's first
+// launch of a shape that another state on the same device prepared takes the
+// answer from here instead of the attribute call and the occupancy query.
+// Entries are never invalid (a kernel's limit only ever rises to the device's
+// maximum); past kShapeCacheEntries the oldest are overwritten.
+constexpr size_t kShapeCacheEntries = 256;
+struct ShapeCache {
+    std::mutex mu;
+    std::vector<std::pair<int, vegas_state::LaunchShape>> v;  // (device, shape)
+    size_t next = 0;
+};
+ShapeCache& shape_cache() {
+    static ShapeCache* c = new ShapeCache;  // never destroyed, as the pinned pool
+    return *c;
+}
+
 // Resident blocks per SM of `kern` launched with (block, smem) on the state's
-// device (current): on the first use of that shape the kernel's dynamic
-// shared-memory limit is raised where needed and the occupancy queried; later
-// iterations read the answer from the state.  The limit is a property of the
+// device (current): on the first use of that shape on the device the kernel's
+// dynamic shared-memory limit is raised where needed and the occupancy
+// queried; later iterations read the answer from the state (or, on a state's
+// first use, from the process-wide cache).  The limit is a property of the
 // kernel, shared by every state that launches it, so it is raised to what a
 // block may use on this device rather than to this shape's size: a state with
 // a smaller histogram can then never lower it under another state's cached
@@ -335,6 +416,23 @@ cudaError_t launch_shape(vegas_state* s, const void* kern, int block, size_t sme
             return cudaSuccess;
         }
     }
+    constexpr int kSlots = (int)(sizeof(s->shapes) / sizeof(s->shapes[0]));
+    auto remember = [&](int o) {
+        const int slot = s->n_shapes < kSlots ? s->n_shapes++ : (s->next_shape++ % kSlots);
+        s->shapes[slot] = {kern, block, smem, o};
+        *occ = o;
+    };
+    ShapeCache& cache = shape_cache();
+    {
+        std::lock_guard<std::mutex> lock(cache.mu);
+        for (const auto& c : cache.v) {
+            if (c.first == s->device && c.second.kern == kern && c.second.block == block &&
+                c.second.smem == smem) {
+                remember(c.second.occ);
+                return cudaSuccess;
+            }
+        }
+    }
     // static shared memory (~0.5 KB) counts against the 48 KB default as well
     cudaError_t e = cudaSuccess;
     if (smem > 40 * 1024)
@@ -343,10 +441,13 @@ cudaError_t launch_shape(vegas_state* s, const void* kern, int block, size_t sme
     int o = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, block, smem);
     if (e != cudaSuccess) return e;
-    constexpr int kSlots = (int)(sizeof(s->shapes) / sizeof(s->shapes[0]));
-    const int slot = s->n_shapes < kSlots ? s->n_shapes++ : (s->next_shape++ % kSlots);
-    s->shapes[slot] = {kern, block, smem, o};
-    *occ = o;
+    remember(o);
+    {
+        std::lock_guard<std::mutex> lock(cache.mu);
+        const std::pair<int, vegas_state::LaunchShape> entry{s->device, {kern, block, smem, o}};
+        if (cache.v.size() < kShapeCacheEntries) cache.v.push_back(entry);
+        else cache.v[cache.next++ % kShapeCacheEntries] = entry;
+    }
     return cudaSuccess;
 }
 
@@ -440,11 +541,12 @@ int vegas_init_grid(vegas_state** out, int dim, int nbins, uint64_t seed, int mo
         mode == VEGAS_FP32_EVAL ? reinterpret_cast<float2*>(s->ws + L.staged) : nullptr;
 
     // pinned staging for reading the log back: the control words and up to
-    // kPinnedLogRows rows (longer logs are read through it in pieces)
-    s->pin_rows = max_iters < kPinnedLogRows ? max_iters : kPinnedLogRows;
-    void* pin = nullptr;
-    if (cudaHostAlloc(&pin, kPinnedCtrlBytes + (size_t)s->pin_rows * kLogStride * sizeof(double),
-                      cudaHostAllocPortable) != cudaSuccess) {
+    // kPinnedLogRows rows (longer logs are read through it in pieces), from
+    // the pool of blocks that destroyed states returned
+    s->pin_rows = pinned_rows(max_iters);
+    s->pin_bytes = kPinnedCtrlBytes + (size_t)s->pin_rows * kLogStride * sizeof(double);
+    void* pin = pinned_take(s->pin_bytes);
+    if (!pin) {
         delete s;
         return VEGAS_ECUDA;
     }
@@ -455,7 +557,7 @@ int vegas_init_grid(vegas_state** out, int dim, int nbins, uint64_t seed, int mo
                                  s->stream));
     if (rc == VEGAS_OK) rc = restage(s);
     if (rc != VEGAS_OK) {
-        cudaFreeHost(pin);
+        pinned_give(pin, s->pin_bytes);  // no copy into it was enqueued
         delete s;
         return rc;
     }
@@ -854,7 +956,8 @@ int vegas_destroy(vegas_state* s) {
     {
         DeviceGuard g(s->device);
         if (g.ok && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = VEGAS_ECUDA;
-        if (s->pin_ctrl && cudaFreeHost(s->pin_ctrl) != cudaSuccess) rc = VEGAS_ECUDA;
+        // copies into the staging are synchronised by the calls that make them
+        if (!pinned_give(s->pin_ctrl, s->pin_bytes)) rc = VEGAS_ECUDA;
     }
     delete s;
     return rc;

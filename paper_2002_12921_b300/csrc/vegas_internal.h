@@ -198,12 +198,14 @@ struct vegas_state {
         int occ;
     } shapes[8];
     int n_shapes, next_shape;
-    // Pinned host staging owned by the descriptor (cudaHostAlloc at creation,
-    // cudaFreeHost in vegas_destroy): the control words, then up to pin_rows
-    // log rows; every read of the log goes through it.
+    // Pinned host staging held by the descriptor (taken from the library's
+    // pool of page-locked blocks at creation, returned to it by vegas_destroy):
+    // the control words, then up to pin_rows log rows; every read of the log
+    // goes through it.
     unsigned* pin_ctrl;
     double* pin_rows_buf;
     int pin_rows;
+    size_t pin_bytes;
 };
 
 // vegas_inject_failure's check, at the start of every enqueueing call: true

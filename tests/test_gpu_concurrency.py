@@ -92,3 +92,49 @@ def test_states_sharing_a_kernel_with_different_shared_memory():
         # the first iteration is on the uniform grid: the same sums to float order
         assert np.allclose(rows[0, 4], ref[0, 4], rtol=1e-6)
         assert np.allclose(rows[:, 4], ref[:, 4], rtol=1e-4)
+
+
+def test_pinned_staging_reused_across_states_and_threads():
+    """Destroyed states return their pinned log staging to the library's pool
+    and new states take it (include/vegas.h, vegas_init_grid): four host
+    threads each create, run, read and destroy 25 states of mixed log lengths
+    (staging sizes of 32, 64 and 128 rows) on their own streams.  Every run's
+    log equals the same run done alone, so no block was ever held by two
+    states at once.  Fixed-grid iterations only, so the sums are
+    deterministic and the logs compared bit for bit."""
+    import paper_2002_12921_b300 as V
+    from paper_2002_12921_b300 import workloads as W
+
+    p = W.gauss_params(3, 0.2)
+    lengths = (3, 20, 40, 70)
+
+    def run(seed, max_iters, stream):
+        with torch.cuda.stream(stream):
+            v = V.Vegas(3, 16, seed, V.VEGAS_FP64, W.GAUSS, p, max_iters=max_iters,
+                        stream=stream)
+            v.run([(60_000 + 1000 * seed, 0)] * 3)
+            rows = v.iterations()
+            v.close()
+        return rows
+
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    ref = {(t, k): run(10 * t + k, lengths[(t + k) % 4], streams[t])
+           for t in range(4) for k in range(5)}
+    errors = []
+
+    def worker(t):
+        try:
+            for c in range(25):
+                k = c % 5
+                rows = run(10 * t + k, lengths[(t + k) % 4], streams[t])
+                if not np.array_equal(rows, ref[(t, k)]):
+                    errors.append((t, c))
+        except Exception as exc:  # reported below
+            errors.append((t, exc))
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join(timeout=600)
+    assert not errors, errors
