@@ -369,7 +369,7 @@ __device__ __forceinline__ void stage_grid(const double* __restrict__ edges, int
 // (the bin's index in the staged grid and in the histogram).  Returns whether the
 // debug build's per-sample checks held (bin index < N, mapped coordinate
 // finite); always true in the release build.
-template <typename R, int D, typename F, typename Sink>
+template <typename R, int D, typename F, typename Sink, int NB = 0>
 __device__ __forceinline__ bool sample_loop(unsigned long long first, unsigned long long end,
                                             unsigned long long stride, unsigned it,
                                             uint32_t c2base, const unsigned (&rk0)[10],
@@ -386,8 +386,10 @@ __device__ __forceinline__ bool sample_loop(unsigned long long first, unsigned l
     // offsets read from the parameters); with more dimensions, or the
     // adapting kernels' extra registers, it recomputes them on the
     // integer-multiply pipe, and the parameter offsets measured faster (d=16
-    // fixed 1371 -> 1330 us, d=8 adapting 121.4 -> 119.2 us per 1e7).
-    constexpr bool kRowOff = D > 8 || Sink::kNeedBins;
+    // fixed 1371 -> 1330 us, d=8 adapting 121.4 -> 119.2 us per 1e7).  With
+    // the bin count compiled in (NB > 0) k N is an immediate at any D: d=12
+    // fixed 1026 -> 977 us, d=16 1306 -> 1262 us per 1e8.
+    constexpr bool kRowOff = (D > 8 && NB == 0) || Sink::kNeedBins;
     const uint32_t t_key = it ^ rk1[0];
     PhiloxCallConst pc[DC];
     bool checks_ok = true;
@@ -670,7 +672,7 @@ __device__ __forceinline__ void iterate_body(const IterArgs& a) {
     __syncthreads();
 
     IterateSink<R, D, ADAPT, ADAPT ? LOGR : -1> sink(shist, N, logr);
-    bool checks_ok = sample_loop<R, D, F>(
+    bool checks_ok = sample_loop<R, D, F, decltype(sink), NB>(
         a.i0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x, a.i0 + a.n_chunk,
         (unsigned long long)gridDim.x * blockDim.x, it, a.integral_id << 8, a.rk0, a.rk1, a.fc,
         N, a.rowoff, (R)j0, n4, nlast, sgrid, sink);
@@ -822,7 +824,9 @@ __global__ void VEGAS_ITERATE_BOUNDS vegas_user_iterate_kernel(const IterArgs a)
     const void* name(int dim) {                                                               \
         static const void* const table[kFixedBinsMaxDim] = {                                  \
             VEGAS_NB(FN, 1), VEGAS_NB(FN, 2), VEGAS_NB(FN, 3), VEGAS_NB(FN, 4),                \
-            VEGAS_NB(FN, 5), VEGAS_NB(FN, 6), VEGAS_NB(FN, 7), VEGAS_NB(FN, 8)};               \
+            VEGAS_NB(FN, 5), VEGAS_NB(FN, 6), VEGAS_NB(FN, 7), VEGAS_NB(FN, 8),                \
+            VEGAS_NB(FN, 9), VEGAS_NB(FN, 10), VEGAS_NB(FN, 11), VEGAS_NB(FN, 12),             \
+            VEGAS_NB(FN, 13), VEGAS_NB(FN, 14), VEGAS_NB(FN, 15), VEGAS_NB(FN, 16)};           \
         if (dim < 1 || dim > kFixedBinsMaxDim) return nullptr;                                \
         return table[dim - 1];                                                                \
     }                                                                                         \

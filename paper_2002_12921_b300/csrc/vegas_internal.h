@@ -126,12 +126,13 @@ const void* iterate_kernel_f32_big(int integrand, int dim);
 // copy count (iterate_kernel_f32's adapting kernels run 32 copies).
 const void* iterate_kernel_f32_few(int integrand, int dim);
 // The float fixed-grid kernels compiled for kFixedBins bins per dimension (the
-// bin count of the paper's workloads here; measured at d = 8: 715 -> 682 us
-// per 1e8 samples, with the bin count a constant of the index arithmetic),
-// for dimensions up to kFixedBinsMaxDim, where that measured faster (above d
-// = 8, and in the adapting kernels, it measured slower).  nullptr otherwise.
+// bin count of the paper's workloads here; measured per 1e8 samples with the
+// bin count a constant of the index arithmetic: d = 8 715 -> 682 us, d = 12
+// 1026 -> 977, d = 16 1306 -> 1262), for dimensions up to kFixedBinsMaxDim
+// (at d = 20 it measured the same, 1593 against 1596 us; in the adapting
+// kernels slower).  nullptr otherwise.
 constexpr int kFixedBins = 50;
-constexpr int kFixedBinsMaxDim = 8;
+constexpr int kFixedBinsMaxDim = 16;
 const void* iterate_kernel_f32_nb(int integrand, int dim);
 const void* iterate_kernel_f64(int integrand, int dim, bool adapt);
 // Shared histogram copies of an adapting iterate block, as log2: 32 copies

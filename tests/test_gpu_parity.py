@@ -783,10 +783,14 @@ def test_pulls_over_seeds_are_standard_normal(mode):
     assert abs(pulls.std() - 1) < 3 / np.sqrt(2 * 200)
 
 
-@pytest.mark.parametrize("fid,dim", [(W.GAUSS, 8), (W.GAUSS, 3), (W.GENZ_PPEAK, 6),
-                                     (W.GAUSS_MIX2, 5)])
+@pytest.mark.parametrize("fid,dim", [(W.GAUSS, 8), (W.GAUSS, 3), (W.GAUSS, 1), (W.GAUSS, 4),
+                                     (W.GENZ_PPEAK, 6), (W.GENZ_PPEAK, 2), (W.GENZ_DISC, 8),
+                                     (W.GENZ_DISC, 5), (W.GAUSS_MIX2, 5), (W.GAUSS_MIX2, 7),
+                                     (W.FLAT, 1), (W.FLAT, 8), (W.GAUSS, 16), (W.GENZ_DISC, 12),
+                                     (W.GAUSS_MIX2, 9), (W.GAUSS, 17)])
 def test_fixed_grid_kernel_compiled_for_50_bins_equals_the_general_one(fid, dim):
-    """Float fixed-grid iterations at 50 bins (up to d = 8) run, under the
+    """Float fixed-grid iterations at 50 bins (up to d = 16; d = 17 takes the
+    general kernel either way) run, under the
     default launch configuration, a kernel with the bin count compiled in; the
     general kernel (taken under an explicit blocks-per-SM setting) gives the
     same sums up to their order of summation, and both equal the oracle's
@@ -795,6 +799,8 @@ def test_fixed_grid_kernel_compiled_for_50_bins_equals_the_general_one(fid, dim)
         p = W.gauss_params(dim, 0.1)
     elif fid == W.GAUSS_MIX2:
         p = W.mix2_params(dim, 0.15)
+    elif fid == W.FLAT:
+        p = []
     else:
         p = W.genz_params(dim, seed=dim, kind=fid)
     e = oracle.run(dim, 50, 9, fid, p, [(100_000, 1)] * 3)["edges"]
