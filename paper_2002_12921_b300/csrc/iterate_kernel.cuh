@@ -573,10 +573,20 @@ struct IterateSink {
                                 got[g] = atomicCAS(reinterpret_cast<B*>(p[g]),
                                                    HistBits<H>::bits(old[g]),
                                                    HistBits<H>::bits(old[g] + (H)fw2));
+                        // one test for the group (any swap that lost a race),
+                        // then the per-add tests only when one did: d=8
+                        // adapting 119.5 -> 116.2 us per 1e7, d=20 238.6 ->
+                        // 232.3 (groups of 8 this way: 119.7, 247.1)
+                        B miss = 0;
 #pragma unroll
                         for (int g = 0; g < G; ++g)
-                            if (k0 + g < D && got[g] != HistBits<H>::bits(old[g]))
-                                atomicAdd(p[g], (H)fw2);
+                            if (k0 + g < D) miss |= got[g] ^ HistBits<H>::bits(old[g]);
+                        if (miss != 0) {
+#pragma unroll
+                            for (int g = 0; g < G; ++g)
+                                if (k0 + g < D && got[g] != HistBits<H>::bits(old[g]))
+                                    atomicAdd(p[g], (H)fw2);
+                        }
                     }
                 } else {
 #pragma unroll
