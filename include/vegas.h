@@ -457,8 +457,11 @@ int vegas_import_state(vegas_state **out, const void *buf, size_t bytes, void *d
  *               library's own (a mismatch means the two were built from
  *               different headers)
  *   prepare     for (mode, adapt, block threads, dynamic shared bytes): raise
- *               the kernel's shared-memory limit if needed and store its
- *               resident blocks per SM in *blocks; returns a cudaError_t value
+ *               the kernel's shared-memory limit if needed (to the device's
+ *               maximum for the kernel, never lower) and store its resident
+ *               blocks per SM in *blocks; returns a cudaError_t value.  The
+ *               state calls it on its first fixed-grid and first adapting
+ *               iteration and keeps the answer
  *   launch      enqueue the kernel of (mode, adapt) with the argument block
  *               `args` on `stream`; returns a cudaError_t value */
 typedef struct {

@@ -71,10 +71,22 @@ template <typename U, int D>
 int user_prepare(int mode, int adapt, int block, size_t smem, int* blocks) {
     const void* k = user_kernel<U, D>(mode, adapt);
     if (!k || !blocks) return (int)cudaErrorInvalidValue;
-    // the static shared memory (~0.5 KB) counts against the 48 KB default too
+    // the static shared memory (~0.5 KB) counts against the 48 KB default too.
+    // The limit goes to the most a block of this kernel may take on the
+    // device, not to this launch's size, so that a state with fewer bins cannot
+    // lower it under another state's launch of the same kernel.
     if (smem > 40 * 1024) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int dev = 0, optin = 0;
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
+        if (e != cudaSuccess) return (int)e;
+        const size_t cap = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes
+                                                               : 0;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(smem > cap ? smem : cap));
         if (e != cudaSuccess) return (int)e;
     }
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, block, smem);

@@ -273,13 +273,7 @@ extern "C" int vegas_gauss_adjoint(vegas_state* s, const double* params, int npa
     const void* kern = adjoint_kernel(s->mode, dim, g);
     const size_t smem = iterate_smem_bytes(s->mode, dim, s->nbins, false, 0);
     int occ = 0;
-    if (smem > 40 * 1024 &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-        rc = VEGAS_ECUDA;
-    if (rc == VEGAS_OK &&
-        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem) != cudaSuccess ||
-         occ < 1))
+    if (prepare_launch(s->device, kern, 256, smem, &occ) != cudaSuccess || occ < 1)
         rc = VEGAS_ECUDA;
     if (rc == VEGAS_OK) {
         // the block partials (2 (d+2) + 1 doubles each) must fit the workspace's area

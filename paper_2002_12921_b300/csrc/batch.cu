@@ -483,14 +483,8 @@ int vegas_batch_iterate(vegas_batch* b, int adapt, double alpha) {
         kern = batch_iterate_kernel_f32_big(b->integrand);
     }
     const size_t smem = iterate_smem_bytes(b->mode, b->max_dim, b->nbins, ad, a.hist_log2r);
-    if (smem > 40 * 1024 &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-        return VEGAS_ECUDA;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) !=
-            cudaSuccess ||
-        occ < 1)
+    if (prepare_launch(b->device, kern, block, smem, &occ) != cudaSuccess || occ < 1)
         return VEGAS_ECUDA;
     long long grid = (long long)b->sm_count * occ;
     if (grid > (long long)b->num_tiles) grid = b->num_tiles;

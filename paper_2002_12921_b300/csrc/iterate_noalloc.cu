@@ -28,7 +28,7 @@ static_assert(kNaBytes == VEGAS_NOALLOC_SCRATCH_BYTES, "scratch size in vegas.h"
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
-constexpr int kNaMaxDevices = 64;
+constexpr int kNaMaxDevices = kMaxDevices;
 std::mutex g_setup_mutex;
 unsigned char* g_scratch_ptr[kNaMaxDevices] = {};
 
@@ -242,13 +242,8 @@ extern "C" int vegas_iterate_noalloc(double* d_edges, int dim, int nbins, uint64
     const void* kern = noalloc_kernel(mode, dim, ad);
     a.log2r = ad ? hist_log2r(mode, dim, nbins) : 0;
     const size_t smem = iterate_smem_bytes(mode, dim, nbins, ad, a.log2r);
-    if (smem > 40 * 1024 &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-        return VEGAS_ECUDA;
     int occ = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem) != cudaSuccess ||
-        occ < 1 ||
+    if (prepare_launch(attr.device, kern, 256, smem, &occ) != cudaSuccess || occ < 1 ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, attr.device) != cudaSuccess)
         return VEGAS_ECUDA;
     long long grid = (long long)((n_samples + 256 * 8 - 1) / (256 * 8));

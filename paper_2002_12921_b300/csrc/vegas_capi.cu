@@ -261,6 +261,77 @@ void combine_rows(const double* rows, int stride, int first_iter, int n, double*
 
 using namespace vegas;
 
+namespace vegas {
+
+namespace {
+// Launch shapes prepared in this process, with their device.  Entries never go
+// stale (a kernel's limit only ever rises, to the device's maximum); past
+// kShapeCacheEntries the oldest are overwritten.  Never destroyed: launches may
+// come from other threads while the process exits.
+constexpr size_t kShapeCacheEntries = 256;
+struct PreparedShape {
+    int device;
+    const void* kern;
+    int block;
+    size_t smem;
+    int occ;
+};
+struct ShapeCache {
+    std::mutex mu;
+    std::vector<PreparedShape> v;
+    size_t next = 0;
+    int optin[kMaxDevices];  // dynamic shared memory a block may take, per device (0: unknown)
+};
+ShapeCache& shape_cache() {
+    static ShapeCache* c = new ShapeCache{};
+    return *c;
+}
+}  // namespace
+
+cudaError_t prepare_launch(int device, const void* kern, int block, size_t smem, int* occ) {
+    if (device < 0 || device >= kMaxDevices || !kern || !occ) return cudaErrorInvalidValue;
+    ShapeCache& cache = shape_cache();
+    int optin = 0;
+    {
+        std::lock_guard<std::mutex> lock(cache.mu);
+        for (const PreparedShape& c : cache.v) {
+            if (c.device == device && c.kern == kern && c.block == block && c.smem == smem) {
+                *occ = c.occ;
+                return cudaSuccess;
+            }
+        }
+        optin = cache.optin[device];
+    }
+    if (optin == 0) {
+        int o = 0;
+        const cudaError_t e =
+            cudaDeviceGetAttribute(&o, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+        if (e != cudaSuccess) return e;
+        // less what the kernels declare statically (reductions, tile index: < 1 KB)
+        optin = o > 1024 ? o - 1024 : 1;
+    }
+    // static shared memory (~0.5 KB) counts against the 48 KB default as well;
+    // the limit goes to the device's maximum, not to this shape's size, so a
+    // smaller shape prepared later can never lower it under a larger one
+    cudaError_t e = cudaSuccess;
+    if (smem > 40 * 1024)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem > (size_t)optin ? (int)smem : optin);
+    int o = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, block, smem);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lock(cache.mu);
+        cache.optin[device] = optin;
+        const PreparedShape entry{device, kern, block, smem, o};
+        if (cache.v.size() < kShapeCacheEntries) cache.v.push_back(entry);
+        else cache.v[cache.next++ % kShapeCacheEntries] = entry;
+    }
+    *occ = o;
+    return cudaSuccess;
+}
+
+}  // namespace vegas
 
 namespace {
 
@@ -383,31 +454,8 @@ const void* kernel_for(const vegas_state* s, bool adapt) {
                                       : iterate_kernel_f64(s->integrand, s->dim, adapt);
 }
 
-// Launch shapes prepared by any state, with their device: a state's first
-// launch of a shape that another state on the same device prepared takes the
-// answer from here instead of the attribute call and the occupancy query.
-// Entries are never invalid (a kernel's limit only ever rises to the device's
-// maximum); past kShapeCacheEntries the oldest are overwritten.
-constexpr size_t kShapeCacheEntries = 256;
-struct ShapeCache {
-    std::mutex mu;
-    std::vector<std::pair<int, vegas_state::LaunchShape>> v;  // (device, shape)
-    size_t next = 0;
-};
-ShapeCache& shape_cache() {
-    static ShapeCache* c = new ShapeCache;  // never destroyed, as the pinned pool
-    return *c;
-}
-
-// Resident blocks per SM of `kern` launched with (block, smem) on the state's
-// device (current): on the first use of that shape on the device the kernel's
-// dynamic shared-memory limit is raised where needed and the occupancy
-// queried; later iterations read the answer from the state (or, on a state's
-// first use, from the process-wide cache).  The limit is a property of the
-// kernel, shared by every state that launches it, so it is raised to what a
-// block may use on this device rather than to this shape's size: a state with
-// a smaller histogram can then never lower it under another state's cached
-// shape.
+// Per-state cache in front of prepare_launch: a state's iterations read their
+// launch shape from the descriptor, with no lock and no runtime call.
 cudaError_t launch_shape(vegas_state* s, const void* kern, int block, size_t smem, int* occ) {
     for (int i = 0; i < s->n_shapes; ++i) {
         const vegas_state::LaunchShape& c = s->shapes[i];
@@ -416,38 +464,13 @@ cudaError_t launch_shape(vegas_state* s, const void* kern, int block, size_t sme
             return cudaSuccess;
         }
     }
-    constexpr int kSlots = (int)(sizeof(s->shapes) / sizeof(s->shapes[0]));
-    auto remember = [&](int o) {
-        const int slot = s->n_shapes < kSlots ? s->n_shapes++ : (s->next_shape++ % kSlots);
-        s->shapes[slot] = {kern, block, smem, o};
-        *occ = o;
-    };
-    ShapeCache& cache = shape_cache();
-    {
-        std::lock_guard<std::mutex> lock(cache.mu);
-        for (const auto& c : cache.v) {
-            if (c.first == s->device && c.second.kern == kern && c.second.block == block &&
-                c.second.smem == smem) {
-                remember(c.second.occ);
-                return cudaSuccess;
-            }
-        }
-    }
-    // static shared memory (~0.5 KB) counts against the 48 KB default as well
-    cudaError_t e = cudaSuccess;
-    if (smem > 40 * 1024)
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem > (size_t)s->smem_optin ? (int)smem : s->smem_optin);
     int o = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, block, smem);
+    const cudaError_t e = prepare_launch(s->device, kern, block, smem, &o);
     if (e != cudaSuccess) return e;
-    remember(o);
-    {
-        std::lock_guard<std::mutex> lock(cache.mu);
-        const std::pair<int, vegas_state::LaunchShape> entry{s->device, {kern, block, smem, o}};
-        if (cache.v.size() < kShapeCacheEntries) cache.v.push_back(entry);
-        else cache.v[cache.next++ % kShapeCacheEntries] = entry;
-    }
+    constexpr int kSlots = (int)(sizeof(s->shapes) / sizeof(s->shapes[0]));
+    const int slot = s->n_shapes < kSlots ? s->n_shapes++ : (s->next_shape++ % kSlots);
+    s->shapes[slot] = {kern, block, smem, o};
+    *occ = o;
     return cudaSuccess;
 }
 
@@ -625,8 +648,16 @@ static int enqueue_iteration(vegas_state* s, uint64_t begin, uint64_t end, int a
     const size_t smem = iterate_smem_bytes(s->mode, s->dim, s->nbins, ad, log2r);
     int occ = 0;
     if (user) {
-        if (s->user.prepare(s->mode, ad ? 1 : 0, block, smem, &occ) != 0 || occ < 1)
-            return VEGAS_ECUDA;
+        // the caller's kernels: prepared on the first iteration of each kind
+        // (fixed or adapting) and kept in the descriptor
+        vegas_state::UserShape& us = s->user_shape[ad ? 1 : 0];
+        if (us.occ < 1 || us.block != block || us.smem != smem) {
+            int o = 0;
+            if (s->user.prepare(s->mode, ad ? 1 : 0, block, smem, &o) != 0 || o < 1)
+                return VEGAS_ECUDA;
+            us = {block, smem, o};
+        }
+        occ = us.occ;
     } else if (launch_shape(s, kern, block, smem, &occ) != cudaSuccess || occ < 1) {
         return VEGAS_ECUDA;
     }
@@ -722,6 +753,7 @@ int vegas_set_user_integrand(vegas_state* s, const vegas_user_integrand* u, cons
         u->args_bytes != sizeof(IterArgs) || !u->prepare || !u->launch)
         return VEGAS_EINVAL;
     s->user = *u;
+    s->user_shape[0] = s->user_shape[1] = {};  // new kernels: prepare them again
     s->fc.user = d_data;
     return VEGAS_OK;
 }

@@ -135,6 +135,17 @@ constexpr int kFixedBins = 50;
 constexpr int kFixedBinsMaxDim = 16;
 const void* iterate_kernel_f32_nb(int integrand, int dim);
 const void* iterate_kernel_f64(int integrand, int dim, bool adapt);
+
+// Devices a process may use with the library (device ordinals below this).
+constexpr int kMaxDevices = 64;
+// Resident blocks per SM of `kern` launched with (block, smem) on `device`,
+// which must be the current device.  The first launch of a (device, kernel,
+// block, smem) shape in the process raises the kernel's dynamic shared-memory
+// limit where smem needs it -- to the most a block may take on the device, so
+// that no caller can lower it under another's launch -- and queries the
+// occupancy; the answer is kept for the process.  Thread-safe.
+cudaError_t prepare_launch(int device, const void* kern, int block, size_t smem, int* occ);
+
 // Shared histogram copies of an adapting iterate block, as log2: 32 copies
 // (one per lane) where they fit in kHistCopyBudget bytes, fewer otherwise.
 constexpr size_t kHistCopyBudget = 52 * 1024;
@@ -184,6 +195,13 @@ struct vegas_state {
     double params[1 + 2 * VEGAS_MAX_DIM];  // the integrand parameters as given
     int nparams;
     vegas_user_integrand user;  // VEGAS_USER: the caller's kernels (launch == NULL: unset)
+    // VEGAS_USER: the launch shape prepared for the fixed-grid [0] and the
+    // adapting [1] kernel (occ 0: not yet)
+    struct UserShape {
+        int block;
+        size_t smem;
+        int occ;
+    } user_shape[2];
     float2* staged32;  // VEGAS_FP32_EVAL: the grid's staged pairs in the workspace, else null
     int has_box;       // integration box [lo, hi] (vegas_set_box); else the unit cube
     double box_lo[VEGAS_MAX_DIM], box_hi[VEGAS_MAX_DIM];

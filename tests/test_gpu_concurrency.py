@@ -138,3 +138,51 @@ def test_pinned_staging_reused_across_states_and_threads():
     for th in threads:
         th.join(timeout=600)
     assert not errors, errors
+
+
+def test_batches_sharing_a_kernel_with_different_shared_memory_on_threads():
+    """Two float batches whose widest integral has d = 16, at 50 and 100 bins,
+    launch the same big-block adapting kernel with different dynamic shared
+    memory (102 KB and 205 KB of histogram copies).  Run concurrently from two
+    host threads on their own streams, every round of each launches (the
+    kernel's limit is raised once, to the device's maximum, and never lowered
+    by the other batch) and reproduces the batch run alone: sample and
+    non-finite counts exactly, the first round's sums (uniform grid) up to the
+    order of the tiles' FP64 atomic adds, the later rounds within float
+    rounding of the refined grids."""
+    import paper_2002_12921_b300 as V
+    from paper_2002_12921_b300 import workloads as W
+
+    dims = [16, 5, 9]
+    ns = [300_000, 120_000, 200_000]
+    params = [W.gauss_params(d, 0.2) for d in dims]
+    streams = [torch.cuda.Stream() for _ in range(2)]
+
+    def run(nbins, stream):
+        with torch.cuda.stream(stream):
+            B = V.VegasBatch(dims, ns, nbins, 21, V.VEGAS_FP32_EVAL, params, max_iters=4,
+                             stream=stream)
+            B.run(4)
+            out = B.log()
+        return out
+
+    alone = [run(nb, streams[i]) for i, nb in enumerate((50, 100))]
+    results, errors = [None, None], []
+
+    def worker(i, nbins):
+        try:
+            for _ in range(5):
+                results[i] = run(nbins, streams[i])
+        except Exception as exc:  # reported below
+            errors.append((i, exc))
+
+    threads = [threading.Thread(target=worker, args=(i, nb)) for i, nb in enumerate((50, 100))]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join(timeout=600)
+    assert not errors, errors
+    for got, ref in zip(results, alone):
+        assert np.array_equal(got[:, :, 2:4], ref[:, :, 2:4])
+        assert np.allclose(got[:, 0, :2], ref[:, 0, :2], rtol=1e-12, atol=0)
+        assert np.allclose(got[:, :, 4], ref[:, :, 4], rtol=1e-4, atol=0)
