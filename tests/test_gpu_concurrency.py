@@ -186,3 +186,29 @@ def test_batches_sharing_a_kernel_with_different_shared_memory_on_threads():
         assert np.array_equal(got[:, :, 2:4], ref[:, :, 2:4])
         assert np.allclose(got[:, 0, :2], ref[:, 0, :2], rtol=1e-12, atol=0)
         assert np.allclose(got[:, :, 4], ref[:, :, 4], rtol=1e-4, atol=0)
+
+
+def test_pinned_pool_overflow_frees_the_surplus():
+    """More live states than the pinned pool keeps (64): 80 states created,
+    iterated and read, then all destroyed (the pool keeps 64 blocks and frees
+    the other 16), then 80 more created from the refilled pool; every log
+    equals a lone run's."""
+    import paper_2002_12921_b300 as V
+    from paper_2002_12921_b300 import workloads as W
+
+    p = W.gauss_params(2, 0.3)
+
+    def make(seed):
+        v = V.Vegas(2, 8, seed, V.VEGAS_FP64, W.GAUSS, p, max_iters=3)
+        v.iterate(20_000, 0)
+        return v
+
+    ref = make(0)
+    want = ref.iterations()
+    ref.close()
+    for _ in range(2):
+        states = [make(0) for _ in range(80)]
+        for v in states:
+            assert np.array_equal(v.iterations(), want)
+        for v in states:
+            v.close()
