@@ -134,7 +134,9 @@ struct AdjointSink {
     }
 };
 
-template <typename R, int D, bool GRAD>
+// NB > 0: the bin count compiled in (it must equal a.nbins), as for the
+// float fixed-grid iterate kernels.
+template <typename R, int D, bool GRAD, int NB = 0>
 __global__ void __launch_bounds__(256) gauss_adjoint_kernel(const AdjointArgs a) {
     using P = Prec<R>;
     using Pair = typename P::Pair;
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(256) gauss_adjoint_kernel(const AdjointArgs a)
     __shared__ unsigned sbad[32];
     __shared__ int s_last;
 
-    const int N = a.nbins;
+    const int N = NB > 0 ? NB : a.nbins;
     Pair* sgrid = reinterpret_cast<Pair*>(smem_raw);
     stage_grid<R, D, false>(a.edges, N, 0, a.fc, sgrid, nullptr);
     R n4, nlast;
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(256) gauss_adjoint_kernel(const AdjointArgs a)
     __syncthreads();
 
     AdjointSink<R, D, GRAD> sink((R)a.two_over_c2, (R)D);
-    sample_loop<R, D, GaussCoords<R, D>>(
+    sample_loop<R, D, GaussCoords<R, D>, AdjointSink<R, D, GRAD>, NB>(
         (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x, a.n,
         (unsigned long long)gridDim.x * blockDim.x, a.iter, 0u, a.rk0, a.rk1, a.fc, N, a.rowoff,
         (R)(sizeof(R) == 4 ? a.fc.C32 : a.fc.C), n4, nlast, sgrid, sink);
@@ -228,6 +230,23 @@ const void* adjoint_kernel(int mode, int dim, bool grad) {
     return (mode == VEGAS_FP32_EVAL ? f32 : f64)[dim - 1][grad ? 1 : 0];
 }
 
+// The float kernels compiled for kFixedBins bins, dimensions up to
+// kFixedBinsMaxDim (nullptr otherwise): d=8 forward 0.714 -> 0.684 ms,
+// backward 0.869 -> 0.828 ms per 1e8.
+#define ADJ_ROW_NB(D)                                                          \
+    {(const void*)&gauss_adjoint_kernel<float, D, false, kFixedBins>,          \
+     (const void*)&gauss_adjoint_kernel<float, D, true, kFixedBins>}
+
+const void* adjoint_kernel_nb(int dim, bool grad) {
+    static const void* const f32[kFixedBinsMaxDim][2] = {
+        ADJ_ROW_NB(1),  ADJ_ROW_NB(2),  ADJ_ROW_NB(3),  ADJ_ROW_NB(4),
+        ADJ_ROW_NB(5),  ADJ_ROW_NB(6),  ADJ_ROW_NB(7),  ADJ_ROW_NB(8),
+        ADJ_ROW_NB(9),  ADJ_ROW_NB(10), ADJ_ROW_NB(11), ADJ_ROW_NB(12),
+        ADJ_ROW_NB(13), ADJ_ROW_NB(14), ADJ_ROW_NB(15), ADJ_ROW_NB(16)};
+    if (dim < 1 || dim > kFixedBinsMaxDim) return nullptr;
+    return f32[dim - 1][grad ? 1 : 0];
+}
+
 }  // namespace
 }  // namespace vegas
 
@@ -271,6 +290,8 @@ extern "C" int vegas_gauss_adjoint(vegas_state* s, const double* params, int npa
     int rc = VEGAS_OK;
     const bool g = grad != 0;
     const void* kern = adjoint_kernel(s->mode, dim, g);
+    if (s->mode == VEGAS_FP32_EVAL && s->nbins == kFixedBins && adjoint_kernel_nb(dim, g))
+        kern = adjoint_kernel_nb(dim, g);
     const size_t smem = iterate_smem_bytes(s->mode, dim, s->nbins, false, 0);
     int occ = 0;
     if (prepare_launch(s->device, kern, 256, smem, &occ) != cudaSuccess || occ < 1)
