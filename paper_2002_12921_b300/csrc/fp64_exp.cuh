@@ -31,9 +31,14 @@ __device__ __forceinline__ double fp64_exp(double x) {
     constexpr double kShifter = 0x1.8p52;
     constexpr double kMaxArg = 0x1.62e42fefa39efp+9;      // ln(DBL_MAX)
     constexpr double kMinArg = -0x1.74910d52d3052p+9;     // below: rounds to 0
-    if (!(x >= kMinArg && x <= kMaxArg)) {               // out of range, or NaN
-        if (x != x) return x;
-        return x > 0.0 ? __longlong_as_double(0x7ff0000000000000ll) : 0.0;
+    // |x| < 708 (high word below that of 708.0) is inside both ends: the
+    // common case is decided on the integer pipe, the exact double compares
+    // (which the FP64 pipe executes) run only for larger |x| or NaN
+    if (((unsigned)__double2hiint(x) & 0x7fffffffu) >= 0x40862000u) {
+        if (!(x >= kMinArg && x <= kMaxArg)) {           // out of range, or NaN
+            if (x != x) return x;
+            return x > 0.0 ? __longlong_as_double(0x7ff0000000000000ll) : 0.0;
+        }
     }
     const double kd = fma(x, kInvLn2By64, kShifter);
     const int k = __double2loint(kd);

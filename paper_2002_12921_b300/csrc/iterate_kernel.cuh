@@ -220,7 +220,11 @@ struct Prec<double> {
         const double e = ::fma(-0x1.ffffffffp-1, w, e0);
         return make_double2(::fma(e, sc, sh), w * sc);
     }
-    static __device__ __forceinline__ bool finite(double v) { return fabs(v) <= DBL_MAX; }
+    // exponent field not all ones, tested on the integer pipe (the same as
+    // fabs(v) <= DBL_MAX, without an FP64 compare)
+    static __device__ __forceinline__ bool finite(double v) {
+        return ((unsigned)__double2hiint(v) & 0x7ff00000u) != 0x7ff00000u;
+    }
     static __device__ __forceinline__ double fma(double x, double y, double z) {
         return ::fma(x, y, z);
     }
