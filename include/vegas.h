@@ -42,6 +42,12 @@
  *
  * Threads.  A state (or batch) is not thread-safe: calls on one state must not
  * run concurrently; different states may be used from different host threads.
+ * What the library shares between states (the pool of pinned log staging, the
+ * prepared launch shapes of its kernels) is guarded internally.
+ *
+ * Devices.  A workspace may live on any CUDA device of ordinal below 64
+ * (VEGAS_MAX_DEVICES); launches on others fail with VEGAS_ECUDA, and
+ * vegas_iterate_noalloc refuses them with VEGAS_EINVAL.
  *
  * CUDA graphs.  vegas_iterate and vegas_refine only enqueue kernels (no host
  * synchronisation), so a schedule of them can be captured from the state's
@@ -115,6 +121,7 @@ extern "C" {
 #define VEGAS_MAX_DIM 20
 #define VEGAS_MAX_BINS 1024
 #define VEGAS_MAX_DIM_X_BINS 8192 /* dim * nbins (shared-memory grid copy) */
+#define VEGAS_MAX_DEVICES 64      /* device ordinals a workspace may live on */
 
 typedef struct vegas_state vegas_state; /* opaque host descriptor */
 

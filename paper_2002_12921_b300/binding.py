@@ -19,6 +19,7 @@ VEGAS_OK, VEGAS_EINVAL, VEGAS_ECUDA, VEGAS_ENONFINITE, VEGAS_ESTATE, VEGAS_ENOSP
 VEGAS_FP64, VEGAS_FP32_EVAL = 0, 1
 VEGAS_GAUSS, VEGAS_GAUSS_MIX2, VEGAS_FLAT, VEGAS_GENZ_DISC, VEGAS_GENZ_PPEAK, VEGAS_USER = range(6)
 VEGAS_MAX_DIM, VEGAS_MAX_BINS, VEGAS_MAX_DIM_X_BINS = 20, 1024, 8192
+VEGAS_MAX_DEVICES = 64
 VEGAS_MAX_SAMPLE_INDEX = 2**64 - 2**33
 VEGAS_NOALLOC_MAX_DIM_X_BINS, VEGAS_NOALLOC_MAX_BLOCKS = 4096, 2048
 LOG_COLUMNS = ("S1", "S2", "n", "nonfinite", "I", "var")

@@ -137,7 +137,7 @@ const void* iterate_kernel_f32_nb(int integrand, int dim);
 const void* iterate_kernel_f64(int integrand, int dim, bool adapt);
 
 // Devices a process may use with the library (device ordinals below this).
-constexpr int kMaxDevices = 64;
+constexpr int kMaxDevices = VEGAS_MAX_DEVICES;
 // Resident blocks per SM of `kern` launched with (block, smem) on `device`,
 // which must be the current device.  The first launch of a (device, kernel,
 // block, smem) shape in the process raises the kernel's dynamic shared-memory

@@ -117,3 +117,23 @@ def test_sample_words_refuses_counts_beyond_the_index_bound(lib):
     rc = lib.vegas_sample_words(1, 0, 0, 0, V.binding.VEGAS_MAX_SAMPLE_INDEX + 1, 4,
                                 ctypes.c_void_p(0x1000), None)
     assert rc == V.VEGAS_EINVAL
+
+
+def test_binding_constants_equal_the_header():
+    """The binding's copies of the header's limits and status codes are the
+    values include/vegas.h defines."""
+    import os
+    import re
+
+    header = open(os.path.join(os.path.dirname(__file__), "..", "include", "vegas.h")).read()
+    defines = {m.group(1): int(m.group(2).rstrip("uUlL"), 0)
+               for m in re.finditer(r"^#define\s+(VEGAS_\w+)\s+(0x[0-9A-Fa-f]+\w*|-?\d+)\b",
+                                    header, re.M)}
+    names = ["VEGAS_MAX_DIM", "VEGAS_MAX_BINS", "VEGAS_MAX_DIM_X_BINS", "VEGAS_MAX_DEVICES",
+             "VEGAS_MAX_SAMPLE_INDEX", "VEGAS_OK", "VEGAS_EINVAL", "VEGAS_ECUDA",
+             "VEGAS_ENONFINITE", "VEGAS_ESTATE", "VEGAS_ENOSPACE", "VEGAS_FP64",
+             "VEGAS_FP32_EVAL", "VEGAS_GAUSS", "VEGAS_GAUSS_MIX2", "VEGAS_FLAT",
+             "VEGAS_GENZ_DISC", "VEGAS_GENZ_PPEAK", "VEGAS_USER"]
+    for n in names:
+        assert n in defines, n
+        assert getattr(V.binding, n) == defines[n], n
