@@ -293,8 +293,11 @@ def run_step_sharded(V, stream, mode, seed, world, fixed_events=None):
 
     v = V.Vegas(DIM, NBINS, seed, mode, V.VEGAS_GAUSS, W.gauss_params(DIM, A),
                 max_iters=IT_ADAPT + IT_FIXED, stream=stream)
-    # the ranks' grids are compared once per step (after the last refinement)
-    sv = ShardedVegas(GpuShardEngine(v), check_every=IT_ADAPT)
+    # the ranks' grids are compared once per step (after the last refinement);
+    # the comparison is read after the timed steps (ShardedVegas.verify), so no
+    # host synchronisation interrupts a step
+    sv = ShardedVegas(GpuShardEngine(v), check_every=IT_ADAPT, defer_checks=True)
+    v.sharded = sv
     for _ in range(IT_ADAPT):
         sv.iterate(N_ADAPT * world, True, ALPHA)
     for _ in range(IT_FIXED):
@@ -348,6 +351,7 @@ def time_mode(V, mode, steps, warmup, seed0, ws, flush, stream, world=1):
     if world > 1:
         res = last.result(IT_ADAPT)
         for v in handles:
+            v.sharded.verify()  # raises GridMismatch if any step's grids diverged
             v.close()
     else:
         res = V.vegas_result(last, IT_ADAPT)

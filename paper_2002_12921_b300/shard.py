@@ -16,7 +16,7 @@ of its grid's bit patterns with MAX, paired with its complement (so one
 16-byte all-reduce gives the largest and the smallest digest), and every rank
 raises ``GridMismatch`` when they differ.  Cost per check: one digest kernel,
 one 16-byte all-reduce and one host read of its result (a stream
-synchronisation).
+synchronisation), or, with ``defer_checks``, no host read until ``verify()``.
 
 An engine is what one rank computes with; it provides
     iterate_range(n, begin, end, adapt), export() -> 1-d tensor,
@@ -127,15 +127,22 @@ class ShardedVegas:
     (NCCL for CUDA tensors, gloo for CPU ones) and refines.  Every iteration
     needs n >= world size.  check_every = k > 0: after every k-th adapting
     iteration the ranks compare grid digests (check_grids); 0: only when
-    check_grids() is called (run() calls it at the end)."""
+    check_grids() is called (run() calls it at the end).
 
-    def __init__(self, engine, group=None, check_every=1):
+    defer_checks=True: a check all-reduces the digests as usual but leaves the
+    result on the device, so no check synchronises the host with the stream in
+    the middle of a schedule; verify() (called by run() at the end) reads every
+    pending result and raises GridMismatch for the first that differs."""
+
+    def __init__(self, engine, group=None, check_every=1, defer_checks=False):
         import torch.distributed as dist
 
         self.engine, self.group, self.dist = engine, group, dist
         self.rank = dist.get_rank(group) if dist.is_initialized() else 0
         self.world = dist.get_world_size(group) if dist.is_initialized() else 1
         self.check_every = check_every
+        self.defer_checks = defer_checks
+        self.pending = []  # (refinements, reduced digest pair) awaiting verify()
         self.refinements = 0
 
     def iterate(self, n, adapt, alpha=1.5):
@@ -156,20 +163,34 @@ class ShardedVegas:
     def check_grids(self):
         """Raise GridMismatch (on every rank) unless all ranks' grids have the
         same digest: one all-reduce of [digest, ~digest] with MAX gives the
-        largest digest and the complement of the smallest."""
-        d = self.engine.grid_digest()
+        largest digest and the complement of the smallest.  With defer_checks
+        the reduced pair is kept for verify() instead of read here."""
+        d = self.engine.grid_digest().clone()
         if self.world > 1:
-            d = d.clone()
             self.dist.all_reduce(d, op=self.dist.ReduceOp.MAX, group=self.group)
+        if self.defer_checks:
+            self.pending.append((self.refinements, d))
+            return
+        self._raise_if_differ(self.refinements, d)
+
+    def verify(self):
+        """Read the deferred checks' results (one host synchronisation) and
+        raise GridMismatch for the first whose digests differ."""
+        pending, self.pending = self.pending, []
+        for refinements, d in pending:
+            self._raise_if_differ(refinements, d)
+
+    def _raise_if_differ(self, refinements, d):
         hi, lo = int(d[0]), ~int(d[1])
         if hi != lo:
             raise GridMismatch(f"rank {self.rank}: grids differ across ranks after "
-                               f"{self.refinements} refinements (digests {lo:#x} .. {hi:#x})")
+                               f"{refinements} refinements (digests {lo:#x} .. {hi:#x})")
 
     def run(self, schedule, alpha=1.5):
         for n, adapt in schedule:
             self.iterate(n, adapt, alpha)
         self.check_grids()
+        self.verify()
 
 
 class VirtualRanks:

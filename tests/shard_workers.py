@@ -73,25 +73,28 @@ class PerturbingEngine(OracleEngine):
             self.e[self.edge] = np.nextafter(self.e[self.edge], 2.0)
 
 
-def gloo_worker(rank, world, port, out_dir, spec, fail_rank, fail_iter, perturb_rank=-1):
+def gloo_worker(rank, world, port, out_dir, spec, fail_rank, fail_iter, perturb_rank=-1,
+                defer=False):
     """One gloo rank: run the sharded schedule and save rows and grid; the rank
     `fail_rank` raises (host side) before its share of iteration `fail_iter`;
     the others record the error their next collective reports.  The rank
     `perturb_rank` moves one edge of its grid by one ulp after the refinement
-    of iteration 1 (every rank must then raise GridMismatch)."""
+    of iteration 1 (every rank must then raise GridMismatch).  defer: the
+    digest checks are deferred and verified once, after the schedule."""
     import torch.distributed as dist
 
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
                             world_size=world, timeout=timedelta(seconds=20))
     eng = (PerturbingEngine(*spec["engine"], at=1) if rank == perturb_rank
            else OracleEngine(*spec["engine"]))
-    sv = ShardedVegas(eng)
+    sv = ShardedVegas(eng, defer_checks=defer)
     try:
         for t, (n, adapt) in enumerate(spec["schedule"]):
             if rank == fail_rank and t == fail_iter:
                 raise RuntimeError("injected failure")
             sv.iterate(n, adapt, spec["alpha"])
         sv.check_grids()
+        sv.verify()
         np.save(os.path.join(out_dir, f"rows{rank}.npy"), eng.rows())
         np.save(os.path.join(out_dir, f"grid{rank}.npy"), eng.grid())
     except Exception:

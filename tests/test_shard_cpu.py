@@ -74,12 +74,13 @@ def _port():
         return s.getsockname()[1]
 
 
-def _spawn(tmp_path, fail_rank=-1, fail_iter=-1, perturb_rank=-1):
+def _spawn(tmp_path, fail_rank=-1, fail_iter=-1, perturb_rank=-1, defer=False):
     spec = {"engine": (3, 20, 4, W.GAUSS, P), "schedule": SCHED, "alpha": 1.5}
     ctx = torch.multiprocessing.get_context("spawn")
     port = _port()
     procs = [ctx.Process(target=gloo_worker, args=(r, 2, port, str(tmp_path), spec, fail_rank,
-                                                   fail_iter, perturb_rank)) for r in range(2)]
+                                                   fail_iter, perturb_rank, defer))
+             for r in range(2)]
     for p in procs:
         p.start()
     for p in procs:
@@ -119,6 +120,26 @@ def test_gloo_grids_that_differ_by_one_ulp_are_detected(tmp_path):
         err = (tmp_path / f"error{r}.txt").read_text()
         assert "GridMismatch" in err and "after 2 refinements" in err, err
         assert not os.path.exists(tmp_path / f"rows{r}.npy")
+
+
+def test_gloo_deferred_checks_report_the_first_divergence(tmp_path):
+    """The same one-ulp divergence with the checks deferred: the ranks finish
+    the schedule without a host read of any digest, and verify() raises
+    GridMismatch on both ranks naming the first check that differed (after
+    the second refinement); without a divergence the deferred run equals the
+    single run."""
+    codes = _spawn(tmp_path, perturb_rank=1, defer=True)
+    assert codes == [0, 0]
+    for r in range(2):
+        err = (tmp_path / f"error{r}.txt").read_text()
+        assert "GridMismatch" in err and "after 2 refinements" in err, err
+        assert "verify" in err
+    ok = tmp_path / "ok"
+    ok.mkdir()
+    assert _spawn(ok, defer=True) == [0, 0]
+    ref = single()
+    for r in range(2):
+        assert_same_as_single(np.load(ok / f"rows{r}.npy"), np.load(ok / f"grid{r}.npy"), ref)
 
 
 def test_virtual_ranks_detect_a_diverged_grid():
