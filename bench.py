@@ -296,7 +296,10 @@ def run_step_sharded(V, stream, mode, seed, world, fixed_events=None):
     # the ranks' grids are compared once per step (after the last refinement);
     # the comparison is read after the timed steps (ShardedVegas.verify), so no
     # host synchronisation interrupts a step
-    sv = ShardedVegas(GpuShardEngine(v), check_every=IT_ADAPT, defer_checks=True)
+    # the five fixed-grid iterations' sums are exchanged together, in one
+    # all-reduce after the last of them (ShardedVegas.flush)
+    sv = ShardedVegas(GpuShardEngine(v), check_every=IT_ADAPT, defer_checks=True,
+                      defer_fixed=True)
     v.sharded = sv
     for _ in range(IT_ADAPT):
         sv.iterate(N_ADAPT * world, True, ALPHA)
@@ -307,6 +310,7 @@ def run_step_sharded(V, stream, mode, seed, world, fixed_events=None):
         e1.record(stream)
         if fixed_events is not None:
             fixed_events.append((e0, e1))
+    sv.flush()
     return v
 
 
@@ -881,12 +885,14 @@ def main():
                        "l2": "256 MiB buffer written between timed steps, outside the step events",
                        "parallelism": (f"one integral sharded over {world} ranks: counter "
                                        "ranges, NCCL all-reduce of S1, S2 and the histogram "
-                                       "per iteration" if world > 1 else "1 GPU")},
+                                       "per adapting iteration, of the fixed-grid rows' "
+                                       "S1, S2 once per step" if world > 1 else "1 GPU")},
             "clocks": clk,
             "e2e": e2e,
-            # sharded: one more kernel per iteration installs the reduced sums,
-            # and one per step digests the grid for the ranks' comparison
-            "gpu_launches": (LAUNCHES_PER_STEP + (IT_ADAPT + IT_FIXED + 1 if world > 1 else 0))
+            # sharded: one more kernel per adapting iteration installs the
+            # reduced sums, one installs the fixed-grid iterations' rows, and
+            # one per step digests the grid for the ranks' comparison
+            "gpu_launches": (LAUNCHES_PER_STEP + (IT_ADAPT + 1 + 1 if world > 1 else 0))
             * args.steps,
             "roofline": roofline,
             "cpu_baseline": cpu,

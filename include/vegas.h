@@ -277,6 +277,27 @@ int vegas_shard_export(vegas_state *s, double *d_buf);
  * recompute its I and var for n_total samples.  Asynchronous. */
 int vegas_shard_import(vegas_state *s, const double *d_buf, uint64_t n_total);
 
+/* Several fixed-grid iterations exchanged at once.  A fixed-grid iteration
+ * changes neither the grid nor the histogram, and the combination (Lepage
+ * 1978 Sec. 2) needs its totals only when the result is read, so the ranks may
+ * run iterations first_iter .. first_iter+count-1 on their own ranges and sum
+ * their rows in one reduction:
+ *   vegas_shard_export_rows  copies each row's {S1, S2, nonfinite} into d_buf
+ *                            (3*count device doubles, row by row);
+ *   vegas_shard_import_rows  replaces the rows' sums by d_buf's totals and
+ *                            recomputes each row's I and var for n_total
+ *                            samples (the same n for every row).
+ * The rows must be logged on the host (first_iter >= 0, count >= 1,
+ * first_iter + count <= iterations enqueued; else VEGAS_ESTATE) and must be
+ * fixed-grid iterations: an adapting iteration's histogram has to be
+ * exchanged (vegas_shard_export / import) before its refinement.  Until the
+ * import, a row holds the rank's own sums (and the float path's pre-scale of
+ * the next iteration follows that partial estimate, which changes only the
+ * float rounding).  Device buffers as for vegas_shard_export; asynchronous. */
+int vegas_shard_export_rows(vegas_state *s, int first_iter, int count, double *d_buf);
+int vegas_shard_import_rows(vegas_state *s, int first_iter, int count, const double *d_buf,
+                            uint64_t n_total);
+
 /* Gradient of the Eq. 1 Gaussian integral with respect to its parameters, by
  * the reparameterised fixed-grid estimator: on the state's current (frozen)
  * grid, sample i of iteration `iter` is regenerated from its Philox counter

@@ -41,7 +41,7 @@ EXPORTED = ("vegas_workspace_bytes", "vegas_init_grid", "vegas_set_config", "veg
             "vegas_set_user_integrand", "vegas_get_iteration_times",
             "vegas_batch_set_tiles_by_dim", "vegas_set_box", "vegas_pipe_peak",
             "vegas_inject_failure", "vegas_batch_init_integrand", "vegas_result_range",
-            "vegas_grid_digest")
+            "vegas_grid_digest", "vegas_shard_export_rows", "vegas_shard_import_rows")
 
 
 class VegasError(RuntimeError):
@@ -110,6 +110,8 @@ def lib():
         L.vegas_iterate_range.argtypes = [vp, u64, u64, u64, i32]
         L.vegas_shard_export.argtypes = [vp, vp]
         L.vegas_shard_import.argtypes = [vp, vp, u64]
+        L.vegas_shard_export_rows.argtypes = [vp, i32, i32, vp]
+        L.vegas_shard_import_rows.argtypes = [vp, i32, i32, vp, u64]
         L.vegas_grid_digest.argtypes = [vp, vp]
         L.vegas_export_state.argtypes = [vp, vp, ctypes.POINTER(sz)]
         L.vegas_import_state.argtypes = [ctypes.POINTER(vp), vp, sz, vp, sz, vp]

@@ -65,19 +65,24 @@ __global__ void init_kernel(double* edges, double* hist, double* log, unsigned* 
     for (int i = tid; i < kCtrlWords; i += nth) ctrl[i] = 0u;
 }
 
-// A log row from summed shard totals: S1, S2, n, nonfinite, I, var.
-__global__ void shard_row_kernel(double* row, const double* totals, unsigned long long n_total) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Log rows from summed shard totals: row r (kLogStride doubles apart) gets
+// S1, S2, n, nonfinite, I, var from totals[3 r .. 3 r + 2] = {S1, S2,
+// nonfinite}.
+__global__ void shard_row_kernel(double* rows, const double* totals, int count,
+                                 unsigned long long n_total) {
     const double n = (double)n_total;
-    const double S1 = totals[0], S2 = totals[1];
-    const double I = S1 / n;
-    const double var = (S2 / n - I * I) / (n - 1.0);
-    row[0] = S1;
-    row[1] = S2;
-    row[2] = n;
-    row[3] = totals[2];
-    row[4] = I;
-    row[5] = var > 0.0 ? var : 0.0;
+    for (int r = threadIdx.x; r < count; r += blockDim.x) {
+        double* row = rows + (size_t)r * kLogStride;
+        const double S1 = totals[3 * r], S2 = totals[3 * r + 1];
+        const double I = S1 / n;
+        const double var = (S2 / n - I * I) / (n - 1.0);
+        row[0] = S1;
+        row[1] = S2;
+        row[2] = n;
+        row[3] = totals[3 * r + 2];
+        row[4] = I;
+        row[5] = var > 0.0 ? var : 0.0;
+    }
 }
 
 // The grid digest of vegas_grid_digest: sum over the edges i of
@@ -115,9 +120,11 @@ cudaError_t launch_grid_digest(const double* edges, int n, unsigned long long* o
     return launch_kernel(grid_digest_kernel, dim3(1), dim3(256), 0, stream, edges, n, out);
 }
 
-cudaError_t launch_shard_row(double* row, const double* totals, unsigned long long n_total,
-                             cudaStream_t stream) {
-    return launch_kernel(shard_row_kernel, dim3(1), dim3(32), 0, stream, row, totals, n_total);
+cudaError_t launch_shard_rows(double* rows, const double* totals, int count,
+                              unsigned long long n_total, cudaStream_t stream) {
+    const int threads = count < 256 ? 32 * ((count + 31) / 32) : 256;
+    return launch_kernel(shard_row_kernel, dim3(1), dim3(threads), 0, stream, rows, totals,
+                         count, n_total);
 }
 
 cudaError_t launch_refine(const RefineArgs& a, cudaStream_t stream) {

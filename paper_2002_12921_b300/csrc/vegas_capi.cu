@@ -798,8 +798,37 @@ int vegas_shard_import(vegas_state* s, const double* d_buf, uint64_t n_total) {
     if (cudaMemcpyAsync(s->hist, d_buf + 3, (size_t)s->dim * s->nbins * sizeof(double),
                         cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
         return VEGAS_ECUDA;
-    return cuda_status(launch_shard_row(s->log + (size_t)(s->host_iters - 1) * kLogStride, d_buf,
-                                        n_total, s->stream));
+    return cuda_status(launch_shard_rows(s->log + (size_t)(s->host_iters - 1) * kLogStride, d_buf,
+                                         1, n_total, s->stream));
+}
+
+int vegas_shard_export_rows(vegas_state* s, int first_iter, int count, double* d_buf) {
+    if (!s || first_iter < 0 || count < 1 || !device_memory_on(d_buf, s->device))
+        return VEGAS_EINVAL;
+    if (first_iter + count > s->host_iters) return VEGAS_ESTATE;
+    DeviceGuard g(s->device);
+    if (!g.ok) return VEGAS_ECUDA;
+    const double* rows = s->log + (size_t)first_iter * kLogStride;
+    // per row {S1, S2} (columns 0, 1) then nonfinite (column 3), 3 doubles apart
+    const size_t pitch = kLogStride * sizeof(double), out = 3 * sizeof(double);
+    if (cudaMemcpy2DAsync(d_buf, out, rows, pitch, 2 * sizeof(double), (size_t)count,
+                          cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess ||
+        cudaMemcpy2DAsync(d_buf + 2, out, rows + 3, pitch, sizeof(double), (size_t)count,
+                          cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
+        return VEGAS_ECUDA;
+    return VEGAS_OK;
+}
+
+int vegas_shard_import_rows(vegas_state* s, int first_iter, int count, const double* d_buf,
+                            uint64_t n_total) {
+    if (!s || first_iter < 0 || count < 1 || n_total < 2 || n_total > VEGAS_MAX_SAMPLE_INDEX ||
+        !device_memory_on(d_buf, s->device))
+        return VEGAS_EINVAL;
+    if (first_iter + count > s->host_iters) return VEGAS_ESTATE;
+    DeviceGuard g(s->device);
+    if (!g.ok) return VEGAS_ECUDA;
+    return cuda_status(launch_shard_rows(s->log + (size_t)first_iter * kLogStride, d_buf, count,
+                                         n_total, s->stream));
 }
 
 int vegas_grid_digest(vegas_state* s, uint64_t* d_out) {

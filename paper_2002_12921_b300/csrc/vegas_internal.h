@@ -162,10 +162,10 @@ cudaError_t launch_stage32(const double* edges, float2* staged, int dim, int nbi
                            const FnConsts& fc, cudaStream_t stream);
 void combine_rows(const double* rows, int stride, int first_iter, int n, double* mean,
                   double* sigma, double* chi2_dof);
-// Install summed shard totals {S1, S2, nonfinite} into a log row with I, var
-// for n_total samples.
-cudaError_t launch_shard_row(double* row, const double* totals, unsigned long long n_total,
-                             cudaStream_t stream);
+// Install summed shard totals {S1, S2, nonfinite} (3 doubles per row) into
+// `count` consecutive log rows, with I, var for n_total samples each.
+cudaError_t launch_shard_rows(double* rows, const double* totals, int count,
+                              unsigned long long n_total, cudaStream_t stream);
 // The 64-bit digest of n edges and its complement into out[0], out[1].
 cudaError_t launch_grid_digest(const double* edges, int n, unsigned long long* out,
                                cudaStream_t stream);

@@ -7,7 +7,9 @@ one sum per iteration of {S1, S2, nonfinite, histogram} (3 + d N doubles);
 after it every rank holds the totals and refines identically, so the grids
 never diverge and the result equals a single device's run up to the order of
 the sums.  (VegasFlow Sec. 3.4 distributes events over devices of one
-machine; this is that split, written for counter-based sampling.)
+machine; this is that split, written for counter-based sampling.)  Fixed-grid
+iterations need no exchange before the combination, so a run of them can
+share one sum of 3 doubles per row (``defer_fixed``).
 
 Identical grids rest on every rank receiving bit-identical totals from the
 all-reduce.  ``ShardedVegas`` checks that they did: after every
@@ -21,7 +23,9 @@ synchronisation), or, with ``defer_checks``, no host read until ``verify()``.
 An engine is what one rank computes with; it provides
     iterate_range(n, begin, end, adapt), export() -> 1-d tensor,
     import_(totals, n), refine(alpha), rows(), grid(),
-    grid_digest() -> int64 tensor [digest, ~digest] on the collective's device.
+    grid_digest() -> int64 tensor [digest, ~digest] on the collective's device,
+and, for deferred fixed-grid exchanges, export_rows(first, count) -> 1-d tensor
+of {S1, S2, nonfinite} per row and import_rows(first, count, totals, n).
 ``GpuShardEngine`` wraps a CUDA ``Vegas`` state (vegas_iterate_range /
 vegas_shard_export / vegas_shard_import / vegas_grid_digest); tests plug in
 CPU engines.
@@ -98,6 +102,25 @@ class GpuShardEngine:
         self.B._check(self.B.lib().vegas_shard_import(self.v.handle, totals.data_ptr(), int(n)),
                       "vegas_shard_import")
 
+    def export_rows(self, first, count):
+        import torch
+
+        buf = torch.empty(3 * count, dtype=torch.float64, device=self.buf.device)
+        self.B._check(self.B.lib().vegas_shard_export_rows(self.v.handle, int(first), int(count),
+                                                            buf.data_ptr()),
+                      "vegas_shard_export_rows")
+        return buf
+
+    def import_rows(self, first, count, totals, n):
+        # the library reads exactly 3 * count doubles of device memory
+        if (totals.numel() != 3 * count or totals.dtype != self.buf.dtype
+                or totals.device != self.buf.device or not totals.is_contiguous()):
+            raise ValueError(f"totals must be a contiguous float64 tensor of {3 * count} "
+                             f"elements on {self.buf.device}")
+        self.B._check(self.B.lib().vegas_shard_import_rows(self.v.handle, int(first), int(count),
+                                                            totals.data_ptr(), int(n)),
+                      "vegas_shard_import_rows")
+
     def refine(self, alpha):
         self.v.refine(alpha)
 
@@ -132,9 +155,17 @@ class ShardedVegas:
     defer_checks=True: a check all-reduces the digests as usual but leaves the
     result on the device, so no check synchronises the host with the stream in
     the middle of a schedule; verify() (called by run() at the end) reads every
-    pending result and raises GridMismatch for the first that differs."""
+    pending result and raises GridMismatch for the first that differs.
 
-    def __init__(self, engine, group=None, check_every=1, defer_checks=False):
+    defer_fixed=True: consecutive fixed-grid iterations of the same n keep their
+    rank-local sums until flush() (called before the next adapting iteration,
+    by run() at the end, and by the caller before reading the log) sums all of
+    their rows in one all-reduce of 3 doubles per row: a fixed-grid iteration
+    changes neither grid nor histogram, so nothing before the combination
+    needs its totals."""
+
+    def __init__(self, engine, group=None, check_every=1, defer_checks=False,
+                 defer_fixed=False):
         import torch.distributed as dist
 
         self.engine, self.group, self.dist = engine, group, dist
@@ -142,14 +173,27 @@ class ShardedVegas:
         self.world = dist.get_world_size(group) if dist.is_initialized() else 1
         self.check_every = check_every
         self.defer_checks = defer_checks
+        self.defer_fixed = defer_fixed
         self.pending = []  # (refinements, reduced digest pair) awaiting verify()
+        self.fixed = None  # [first row, count, n] of fixed-grid rows awaiting flush()
+        self.iterations = 0
         self.refinements = 0
 
     def iterate(self, n, adapt, alpha=1.5):
         if n < self.world:
             raise ValueError("need at least one sample per rank")
         begin, end = shard_range(n, self.rank, self.world)
+        if adapt or not self.defer_fixed or (self.fixed is not None and self.fixed[2] != n):
+            self.flush()
         self.engine.iterate_range(n, begin, end, adapt)
+        t = self.iterations
+        self.iterations += 1
+        if not adapt and self.defer_fixed:
+            if self.fixed is None:
+                self.fixed = [t, 1, n]
+            else:
+                self.fixed[1] += 1
+            return
         totals = self.engine.export()
         if self.world > 1:
             self.dist.all_reduce(totals, op=self.dist.ReduceOp.SUM, group=self.group)
@@ -159,6 +203,17 @@ class ShardedVegas:
             self.refinements += 1
             if self.check_every and self.refinements % self.check_every == 0:
                 self.check_grids()
+
+    def flush(self):
+        """Exchange the deferred fixed-grid rows (one all-reduce), if any."""
+        if self.fixed is None:
+            return
+        first, count, n = self.fixed
+        self.fixed = None
+        totals = self.engine.export_rows(first, count)
+        if self.world > 1:
+            self.dist.all_reduce(totals, op=self.dist.ReduceOp.SUM, group=self.group)
+        self.engine.import_rows(first, count, totals, n)
 
     def check_grids(self):
         """Raise GridMismatch (on every rank) unless all ranks' grids have the
@@ -189,6 +244,7 @@ class ShardedVegas:
     def run(self, schedule, alpha=1.5):
         for n, adapt in schedule:
             self.iterate(n, adapt, alpha)
+        self.flush()
         self.check_grids()
         self.verify()
 

@@ -37,8 +37,9 @@ def test_two_ranks_shard_the_headline_integral():
     line = json.loads(lines[0])
     assert line["n_gpus"] == 2 and line["scaling"] == "weak" and line["steps"] == 2
     assert line["value"] > 0 and line["e2e"]["value"] > 0
-    # 27 launches per step, one sum-installing launch per iteration (15) and
-    # one grid digest per step for the ranks' comparison
-    assert line["gpu_launches"] == (27 + 15 + 1) * 2
+    # 27 launches per step, one sum-installing launch per adapting iteration
+    # (10), one for the five fixed-grid rows together and one grid digest per
+    # step for the ranks' comparison
+    assert line["gpu_launches"] == (27 + 10 + 1 + 1) * 2
     res = line["result"]["fp32"]
     assert abs(res["mean"] - line["result"]["exact"]) < 6 * res["sigma"]

@@ -8,7 +8,8 @@ import pytest
 import oracle
 import paper_2002_12921_b300 as V
 from paper_2002_12921_b300 import workloads as W
-from paper_2002_12921_b300.shard import GpuShardEngine, RankFailure, VirtualRanks
+from paper_2002_12921_b300.shard import (GpuShardEngine, RankFailure, VirtualRanks,
+                                         shard_range)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -128,6 +129,8 @@ def test_host_buffers_are_refused_where_device_memory_is_required():
     L = V.lib()
     assert L.vegas_shard_export(v.handle, hp) == V.VEGAS_EINVAL
     assert L.vegas_shard_import(v.handle, hp, 10_000) == V.VEGAS_EINVAL
+    assert L.vegas_shard_export_rows(v.handle, 0, 1, hp) == V.VEGAS_EINVAL
+    assert L.vegas_shard_import_rows(v.handle, 0, 1, hp, 10_000) == V.VEGAS_EINVAL
     assert L.vegas_grid_digest(v.handle, hp) == V.VEGAS_EINVAL
     p = (ctypes.c_double * 4)(*W.gauss_params(3, 0.1))
     assert L.vegas_gauss_adjoint(v.handle, p, 4, 0, 10_000, 1, hp) == V.VEGAS_EINVAL
@@ -138,3 +141,46 @@ def test_host_buffers_are_refused_where_device_memory_is_required():
     assert np.all(host == 0.0)
     assert v.iterations().shape[0] == 1
     v.close()
+
+
+def test_gpu_fixed_rows_exchanged_together_equal_oracle():
+    """Two virtual ranks exchange an adapting iteration at once and then three
+    fixed-grid iterations in one sum of their rows (vegas_shard_export_rows /
+    vegas_shard_import_rows): every row equals the FP64 oracle's run, as with
+    one exchange per iteration; rows outside the log are refused."""
+    import ctypes
+
+    sched = [(300_000, 1), (200_001, 0), (200_001, 0), (200_001, 0)]
+    states = [V.Vegas(6, 40, 21, V.VEGAS_FP64, W.GAUSS, P, max_iters=8) for _ in range(2)]
+    engs = [GpuShardEngine(s) for s in states]
+    n = sched[0][0]
+    for r, e in enumerate(engs):
+        e.iterate_range(n, *shard_range(n, r, 2), True)
+    tot = engs[0].export().clone() + engs[1].export().clone()
+    for e in engs:
+        e.import_(tot, n)
+        e.refine(1.5)
+    n = sched[1][0]
+    for _ in range(3):
+        for r, e in enumerate(engs):
+            e.iterate_range(n, *shard_range(n, r, 2), False)
+    rows = engs[0].export_rows(1, 3).clone() + engs[1].export_rows(1, 3).clone()
+    for e in engs:
+        e.import_rows(1, 3, rows, n)
+    ref = oracle.run(6, 40, 21, W.GAUSS, P, sched, nthreads=8)
+    buf = torch.zeros(12, dtype=torch.float64, device="cuda")
+    L = V.lib()
+    assert L.vegas_shard_export_rows(states[0].handle, 2, 3, ctypes.c_void_p(buf.data_ptr())) \
+        == V.VEGAS_ESTATE
+    assert L.vegas_shard_import_rows(states[0].handle, -1, 1, ctypes.c_void_p(buf.data_ptr()),
+                                     n) == V.VEGAS_EINVAL
+    for s in states:
+        got = s.iterations()
+        assert got.shape[0] == 4
+        for t, r in enumerate(ref["log"]):
+            tol = 1e-12 if t == 0 else fp64_tol(ref["grids"][t])
+            assert got[t][2] == sched[t][0]
+            assert abs(got[t][4] - r["I"]) <= tol * abs(r["I"]), t
+            assert abs(got[t][5] - r["var"]) <= 1e3 * tol * r["var"], t
+        assert np.allclose(s.grid(), ref["edges"], rtol=1e-12, atol=1e-15)
+        s.close()

@@ -9,7 +9,7 @@ import torch
 
 import oracle
 from paper_2002_12921_b300 import workloads as W
-from paper_2002_12921_b300.shard import (GridMismatch, RankFailure, VirtualRanks,
+from paper_2002_12921_b300.shard import (GridMismatch, RankFailure, ShardedVegas, VirtualRanks,
                                          grid_digest_host, shard_range)
 from tests.shard_workers import OracleEngine, PerturbingEngine, gloo_worker
 
@@ -17,13 +17,19 @@ P = W.gauss_params(3, 0.15, [0.4, 0.5, 0.6])
 SCHED = [(30_000, 1), (30_000, 1), (20_000, 1), (40_001, 0)]
 
 
-def single():
-    return oracle.run(3, 20, 4, W.GAUSS, P, SCHED)
+# fixed-grid runs of two lengths, an adapting iteration between them
+SCHED_F = [(30_000, 1), (20_000, 0), (20_000, 0), (25_000, 1), (40_001, 0), (40_001, 0),
+           (30_000, 0)]
 
 
-def assert_same_as_single(rows, grid, ref):
+def single(sched=SCHED):
+    return oracle.run(3, 20, 4, W.GAUSS, P, sched)
+
+
+def assert_same_as_single(rows, grid, ref, sched=SCHED):
+    assert len(rows) == len(sched)
     for t, r in enumerate(ref["log"]):
-        assert rows[t][2] == SCHED[t][0]
+        assert rows[t][2] == sched[t][0]
         assert abs(rows[t][4] - r["I"]) <= 1e-12 * abs(r["I"]), t
         assert abs(rows[t][5] - r["var"]) <= 1e-10 * r["var"], t
     assert np.allclose(grid, ref["edges"], rtol=1e-12, atol=1e-15)
@@ -74,12 +80,13 @@ def _port():
         return s.getsockname()[1]
 
 
-def _spawn(tmp_path, fail_rank=-1, fail_iter=-1, perturb_rank=-1, defer=False):
-    spec = {"engine": (3, 20, 4, W.GAUSS, P), "schedule": SCHED, "alpha": 1.5}
+def _spawn(tmp_path, fail_rank=-1, fail_iter=-1, perturb_rank=-1, defer=False,
+           defer_fixed=False, sched=SCHED):
+    spec = {"engine": (3, 20, 4, W.GAUSS, P), "schedule": sched, "alpha": 1.5}
     ctx = torch.multiprocessing.get_context("spawn")
     port = _port()
     procs = [ctx.Process(target=gloo_worker, args=(r, 2, port, str(tmp_path), spec, fail_rank,
-                                                   fail_iter, perturb_rank, defer))
+                                                   fail_iter, perturb_rank, defer, defer_fixed))
              for r in range(2)]
     for p in procs:
         p.start()
@@ -140,6 +147,37 @@ def test_gloo_deferred_checks_report_the_first_divergence(tmp_path):
     ref = single()
     for r in range(2):
         assert_same_as_single(np.load(ok / f"rows{r}.npy"), np.load(ok / f"grid{r}.npy"), ref)
+
+
+def test_gloo_deferred_fixed_rows_equal_single_run(tmp_path):
+    """Fixed-grid iterations exchanged in groups (ShardedVegas defer_fixed:
+    each group of consecutive fixed-grid iterations of one n in one
+    all-reduce, flushed before the next adapting iteration, on a change of n
+    and at the end): the two ranks' logs and grids equal the single run's, in
+    both layouts of the schedule, as with one exchange per iteration."""
+    for sched in (SCHED_F, SCHED):
+        out = tmp_path / f"s{len(sched)}"
+        out.mkdir()
+        assert _spawn(out, defer_fixed=True, sched=sched) == [0, 0]
+        ref = single(sched)
+        for r in range(2):
+            assert_same_as_single(np.load(out / f"rows{r}.npy"), np.load(out / f"grid{r}.npy"),
+                                  ref, sched)
+
+
+def test_deferred_fixed_rows_single_process():
+    """World size 1 (no process group): the deferred rows hold the rank's own
+    sums until flush(), which installs the same totals a per-iteration
+    exchange gives."""
+    a, b = OracleEngine(3, 20, 4, W.GAUSS, P), OracleEngine(3, 20, 4, W.GAUSS, P)
+    sa, sb = ShardedVegas(a, defer_fixed=True), ShardedVegas(b)
+    for n, adapt in SCHED_F[:3]:
+        sa.iterate(n, adapt)
+        sb.iterate(n, adapt)
+    assert sa.fixed == [1, 2, 20_000] and np.isnan(a.rows()[1, 4])
+    sa.flush()
+    assert sa.fixed is None
+    assert np.array_equal(a.rows(), b.rows())
 
 
 def test_virtual_ranks_detect_a_diverged_grid():
