@@ -98,6 +98,11 @@ static void capi_host_paths(void) {
     CHECK(vegas_iterate(NULL, 1000, 1) == VEGAS_EINVAL);
     CHECK(vegas_refine(NULL, 1.5) == VEGAS_EINVAL);
     CHECK(vegas_set_user_integrand(NULL, NULL, NULL) == VEGAS_EINVAL);
+    CHECK(vegas_shard_export(NULL, NULL) == VEGAS_EINVAL);
+    CHECK(vegas_shard_import(NULL, NULL, 10) == VEGAS_EINVAL);
+    CHECK(vegas_shard_export_rows(NULL, 0, 1, NULL) == VEGAS_EINVAL);
+    CHECK(vegas_shard_import_rows(NULL, 0, 1, NULL, 10) == VEGAS_EINVAL);
+    CHECK(vegas_grid_digest(NULL, NULL) == VEGAS_EINVAL);
 
     /* checkpoint blobs: wrong magic, truncated header, truncated body */
     unsigned char blob[512];
