@@ -2,20 +2,21 @@
 // Tang, "Table-driven implementation of the exponential function in IEEE
 // floating-point arithmetic", ACM TOMS 15(2), 1989.
 //
-//   x = (64 m + j) ln2/64 + r,  j in [0, 63],  |r| <= ln2/128
-//   e^x = 2^m * 2^(j/64) * e^r
+//   x = (256 m + j) ln2/256 + r,  j in [0, 255],  |r| <= ln2/512
+//   e^x = 2^m * 2^(j/256) * e^r
 //
-// k = 64 m + j is x * 64/ln2 rounded to the nearest integer (by adding and
+// k = 256 m + j is x * 256/ln2 rounded to the nearest integer (by adding and
 // subtracting 1.5 * 2^52, which also leaves k in the low word); r is reduced
-// with ln2/64 split in two (the high part has 17 trailing zero bits, so k times
-// it is exact for |k| < 2^17); e^r - 1 is its Taylor polynomial to degree 5
-// (the omitted r^6/720 is below 3.5e-17 for |r| <= ln2/128); 2^(j/64) comes
-// from a 64-entry table of correctly rounded doubles; 2^m is added to the
-// exponent field (two multiplications at the ends of the range).  About 10
-// double-precision operations; alone it ran 1.33x as fast as the CUDA
-// library's exp, inside the FP64 iterate kernel 1% (8.03 -> 7.94 ms per 1e8 at
-// d=8).  Agreement with the CUDA library's and numpy's exp to 2 ulp over the
-// whole range, and the special values, are tested.
+// with ln2/256 split in two (the high part has 19 trailing zero bits, so k
+// times it is exact for |k| < 2^19, which |x| < 746 keeps); e^r - 1 is its
+// Taylor polynomial to degree 4 (the omitted r^5/120 is below 3.9e-17 for
+// |r| <= ln2/512); 2^(j/256) comes from a 256-entry table of correctly
+// rounded doubles; 2^m is added to the exponent field (two multiplications at
+// the ends of the range).  About 9 double-precision operations; with 64
+// entries and degree 5 it ran 1.33x as fast as the CUDA library's exp, inside
+// the FP64 iterate kernel 1% (8.03 -> 7.94 ms per 1e8 at d=8).  Agreement with
+// the CUDA library's and numpy's exp to 2 ulp over the whole range, and the
+// special values, are tested.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,9 +26,9 @@
 namespace vegas {
 
 __device__ __forceinline__ double fp64_exp(double x) {
-    constexpr double kInvLn2By64 = 0x1.71547652b82fep+6;  // 64 / ln 2
-    constexpr double kLn2By64Hi = 0x1.62e42fefa0000p-7;   // ln 2 / 64, high part
-    constexpr double kLn2By64Lo = 0x1.cf79abc9e3b3ap-46;  // ln 2 / 64 - high part
+    constexpr double kInvLn2By256 = 0x1.71547652b82fep+8;  // 256 / ln 2
+    constexpr double kLn2By256Hi = 0x1.62e42fef80000p-9;   // ln 2 / 256, high part
+    constexpr double kLn2By256Lo = 0x1.1cf79abc9e3b4p-44;  // ln 2 / 256 - high part
     constexpr double kShifter = 0x1.8p52;
     constexpr double kMaxArg = 0x1.62e42fefa39efp+9;      // ln(DBL_MAX)
     constexpr double kMinArg = -0x1.74910d52d3052p+9;     // below: rounds to 0
@@ -40,21 +41,20 @@ __device__ __forceinline__ double fp64_exp(double x) {
             return x > 0.0 ? __longlong_as_double(0x7ff0000000000000ll) : 0.0;
         }
     }
-    const double kd = fma(x, kInvLn2By64, kShifter);
+    const double kd = fma(x, kInvLn2By256, kShifter);
     const int k = __double2loint(kd);
     // = kd - kShifter exactly; the conversion instead of a double subtraction
     // measured 0.4% faster in the FP64 kernels (7.676 -> 7.645 ms per 1e8)
     const double kf = __int2double_rn(k);
-    double r = fma(-kf, kLn2By64Hi, x);
-    r = fma(-kf, kLn2By64Lo, r);
-    double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-    p = fma(p, r, 1.0 / 6.0);
+    double r = fma(-kf, kLn2By256Hi, x);
+    r = fma(-kf, kLn2By256Lo, r);
+    double p = fma(r, 1.0 / 24.0, 1.0 / 6.0);
     p = fma(p, r, 0.5);
     p = fma(p, r, 1.0);
     p *= r;                                      // e^r - 1
-    const double t = __ldg(&kExp2Over64[k & 63]);
-    const double y = fma(t, p, t);               // 2^(j/64) e^r in [0.994, 1.99)
-    const int m = k >> 6;                        // arithmetic shift: floor(k / 64)
+    const double t = __ldg(&kExp2Table[k & 255]);
+    const double y = fma(t, p, t);               // 2^(j/256) e^r in [0.998, 1.998)
+    const int m = k >> 8;                        // arithmetic shift: floor(k / 256)
     if (m >= -1021 && m <= 1023)                 // normal result: scale the exponent
         return __hiloint2double(__double2hiint(y) + m * (1 << 20), __double2loint(y));
     // near the ends (subnormal result, or m = 1024 just below ln DBL_MAX): two

@@ -95,17 +95,17 @@ def test_user_integrand_descriptors_load_without_a_device(lib):
 
 
 def test_fp64_exp_table_is_correctly_rounded_powers_of_two():
-    """The 64-entry table of the FP64 path's exponential holds 2^(j/64) rounded
-    to the nearest double (checked against 200-bit arithmetic)."""
+    """The 256-entry table of the FP64 path's exponential holds 2^(j/256)
+    rounded to the nearest double (checked against 200-bit arithmetic)."""
     import mpmath
 
     mpmath.mp.prec = 200
     path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                         "paper_2002_12921_b300", "csrc", "exp2_table.h")
     vals = [float.fromhex(h) for h in re.findall(r"0x[0-9a-f.]+p[+-]\d+", open(path).read())]
-    assert len(vals) == 64
+    assert len(vals) == 256
     for j, v in enumerate(vals):
-        exact = mpmath.mpf(2) ** (mpmath.mpf(j) / 64)
+        exact = mpmath.mpf(2) ** (mpmath.mpf(j) / 256)
         assert abs(mpmath.mpf(v) - exact) <= mpmath.mpf(np.spacing(v)) / 2, j
 
 
