@@ -298,7 +298,7 @@ def run_step_sharded(V, stream, mode, seed, world, fixed_events=None):
     # host synchronisation interrupts a step
     # the five fixed-grid iterations' sums are exchanged together, in one
     # all-reduce after the last of them (ShardedVegas.flush)
-    sv = ShardedVegas(GpuShardEngine(v), check_every=IT_ADAPT, defer_checks=True,
+    sv = ShardedVegas(GpuShardEngine(v, logged=0), check_every=IT_ADAPT, defer_checks=True,
                       defer_fixed=True)
     v.sharded = sv
     for _ in range(IT_ADAPT):

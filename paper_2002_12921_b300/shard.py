@@ -21,7 +21,8 @@ one 16-byte all-reduce and one host read of its result (a stream
 synchronisation), or, with ``defer_checks``, no host read until ``verify()``.
 
 An engine is what one rank computes with; it provides
-    iterate_range(n, begin, end, adapt), export() -> 1-d tensor,
+    iterate_range(n, begin, end, adapt) -> the iteration's log row,
+    export() -> 1-d tensor,
     import_(totals, n), refine(alpha), rows(), grid(),
     grid_digest() -> int64 tensor [digest, ~digest] on the collective's device,
 and, for deferred fixed-grid exchanges, export_rows(first, count) -> 1-d tensor
@@ -67,7 +68,9 @@ def shard_range(n, rank, world):
 class GpuShardEngine:
     """A rank's engine over a CUDA ``Vegas`` state."""
 
-    def __init__(self, vegas):
+    def __init__(self, vegas, logged=None):
+        """logged: the log rows the state already holds (0 for a new state);
+        None reads them from the state (one stream synchronisation)."""
         import torch
 
         from . import binding as B
@@ -76,8 +79,11 @@ class GpuShardEngine:
         self.buf = torch.zeros(3 + vegas.dim * vegas.nbins, dtype=torch.float64,
                                device=vegas.workspace.device)
         self.digest = torch.zeros(2, dtype=torch.int64, device=vegas.workspace.device)
+        # log rows the state already holds (a resumed state continues after them)
+        self.logged = len(vegas.iterations()) if logged is None else int(logged)
 
     def iterate_range(self, n, begin, end, adapt):
+        """Enqueue this rank's range; returns the iteration's log row."""
         rc = self.B.lib().vegas_iterate_range(self.v.handle, int(n), int(begin), int(end),
                                               1 if adapt else 0)
         if rc == self.B.VEGAS_ECUDA:
@@ -87,6 +93,8 @@ class GpuShardEngine:
             # the iteration's log row and count are written only on success
             raise RankFailure("vegas_iterate_range: " + self.B.lib().vegas_strerror(rc).decode())
         self.B._check(rc, "vegas_iterate_range")
+        self.logged += 1
+        return self.logged - 1
 
     def export(self):
         self.B._check(self.B.lib().vegas_shard_export(self.v.handle, self.buf.data_ptr()),
@@ -176,7 +184,6 @@ class ShardedVegas:
         self.defer_fixed = defer_fixed
         self.pending = []  # (refinements, reduced digest pair) awaiting verify()
         self.fixed = None  # [first row, count, n] of fixed-grid rows awaiting flush()
-        self.iterations = 0
         self.refinements = 0
 
     def iterate(self, n, adapt, alpha=1.5):
@@ -185,9 +192,7 @@ class ShardedVegas:
         begin, end = shard_range(n, self.rank, self.world)
         if adapt or not self.defer_fixed or (self.fixed is not None and self.fixed[2] != n):
             self.flush()
-        self.engine.iterate_range(n, begin, end, adapt)
-        t = self.iterations
-        self.iterations += 1
+        t = self.engine.iterate_range(n, begin, end, adapt)  # the iteration's log row
         if not adapt and self.defer_fixed:
             if self.fixed is None:
                 self.fixed = [t, 1, n]

@@ -37,6 +37,7 @@ class OracleEngine:
         p = self.part
         self._rows.append([p["S1"], p["S2"], end - begin, float(p["nonfinite"]), np.nan, np.nan])
         self.it += 1
+        return len(self._rows) - 1
 
     def export(self):
         p = self.part

@@ -184,3 +184,31 @@ def test_gpu_fixed_rows_exchanged_together_equal_oracle():
             assert abs(got[t][5] - r["var"]) <= 1e3 * tol * r["var"], t
         assert np.allclose(s.grid(), ref["edges"], rtol=1e-12, atol=1e-15)
         s.close()
+
+
+def test_deferred_fixed_rows_after_earlier_iterations():
+    """A state that already logged iterations before ShardedVegas took it over
+    (the engine reads how many): with defer_fixed, the next fixed-grid rows
+    are exchanged into their own rows, and the log equals the same schedule
+    run on one state call by call."""
+    from paper_2002_12921_b300.shard import ShardedVegas
+
+    sched = [(200_000, 1), (200_000, 1), (150_001, 0), (150_001, 0), (150_001, 0)]
+    a = V.Vegas(6, 40, 9, V.VEGAS_FP64, W.GAUSS, P, max_iters=8)
+    b = V.Vegas(6, 40, 9, V.VEGAS_FP64, W.GAUSS, P, max_iters=8)
+    for n, adapt in sched[:2]:
+        a.iterate(n, 1)
+        a.refine(1.5)
+    sv = ShardedVegas(GpuShardEngine(a), defer_fixed=True)
+    assert sv.engine.logged == 2
+    for n, adapt in sched[2:]:
+        sv.iterate(n, adapt)
+    assert sv.fixed == [2, 3, 150_001]
+    sv.flush()
+    b.run(sched)
+    ra, rb = a.iterations(), b.iterations()
+    assert ra.shape == rb.shape == (5, 6)
+    assert np.array_equal(ra[:, 2:4], rb[:, 2:4])
+    assert np.allclose(ra[:, [0, 1, 4, 5]], rb[:, [0, 1, 4, 5]], rtol=1e-13, atol=0)
+    a.close()
+    b.close()
