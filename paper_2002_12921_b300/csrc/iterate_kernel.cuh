@@ -564,12 +564,13 @@ struct IterateSink {
                     // The loads and swaps address the lane's copy by its 32-bit
                     // shared-memory address (one shift-and-add per add): d=16
                     // adapting 199.5 -> 193.7 us per 1e7, the 256-integral
-                    // batch round 6.04 -> 5.86 ms, d=8 unchanged.
+                    // batch's 8 iterations 6.04 -> 5.86 ms, d=8 unchanged.
                     using B = typename HistBits<H>::type;
                     const int sh = (LOGR >= 0 ? LOGR : logr) + 2;  // bytes per bin: 4 << logr
                     // one group of up to 8 dimensions where d <= 8 (d=8 116.6 ->
                     // 113.6 us per 1e7), groups of 4 above (groups of 8 there:
-                    // d=16 193.7 -> 196.0, the batch round 5.86 -> 6.10 ms)
+                    // d=16 193.7 -> 196.0, the batch's 8 iterations 5.86 ->
+                    // 6.10 ms)
                     constexpr int G = D <= 8 ? 8 : 4;
 #pragma unroll
                     for (int k0 = 0; k0 < D; k0 += G) {
