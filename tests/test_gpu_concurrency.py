@@ -212,3 +212,35 @@ def test_pinned_pool_overflow_frees_the_surplus():
             assert np.array_equal(v.iterations(), want)
         for v in states:
             v.close()
+
+
+def test_log_longer_than_the_pinned_staging_is_read_in_pieces():
+    """A log of 4500 rows, longer than the 4096 rows a state's pinned staging
+    holds, is read back through it in pieces (vegas_get_iterations and
+    vegas_result); the rows equal the log copied straight from the device by
+    vegas_export_state (blob: 16 header words, the parameters, grid,
+    histogram, then 8 doubles per row), and the combined result equals the
+    combination of those rows."""
+    import struct
+
+    import oracle
+    import paper_2002_12921_b300 as V
+    from paper_2002_12921_b300 import workloads as W
+
+    dim, nbins, iters, n = 2, 8, 4500, 1000
+    p = W.gauss_params(dim, 0.3)
+    v = V.Vegas(dim, nbins, 3, V.VEGAS_FP64, W.GAUSS, p, max_iters=iters)
+    for _ in range(iters):
+        v.iterate(n, 0)
+    rows = v.iterations()
+    mean, sigma, chi2, n_iter, _ = v.result(0)
+    blob = v.export_state()
+    v.close()
+    (np_,) = struct.unpack_from("<Q", blob, 56)
+    off = 8 * (16 + np_ + dim * (nbins + 1) + dim * nbins)
+    log = np.frombuffer(blob, dtype="<f8", count=iters * 8, offset=off).reshape(iters, 8)
+    assert rows.shape == (iters, 6) and n_iter == iters
+    assert np.array_equal(rows, log[:, :6])
+    assert np.all(rows[:, 2] == n)
+    m, s, c = oracle.combine(list(log[:, 4]), list(log[:, 5]))
+    assert abs(mean - m) <= 1e-12 * abs(m) and abs(sigma - s) <= 1e-12 * s
