@@ -683,18 +683,23 @@ def cpu_baseline(fast=False):
                                   f"adapting iteration (the GPU's launch size), {cores} threads"}
         # the oracle's rate against its thread count (the paper's CPU scaling
         # with cores, Sec. 3.3-3.4): one fixed-grid d=8 iteration of 1e7
-        # samples on the uniform grid per thread count
+        # samples on the uniform grid per thread count, the better of two runs
+        # (the host is shared, so a single run can catch another job's load)
         sweep, t = {}, 1
         e8 = oracle.uniform_grid(DIM, NBINS)
         while t <= cores:
-            t0 = time.perf_counter()
-            oracle.iterate(e8, 2, 0, N_ADAPT, W.GAUSS, W.gauss_params(DIM, A), False,
-                           nthreads=t)
-            sweep[str(t)] = N_ADAPT / (time.perf_counter() - t0)
+            best = 0.0
+            for _ in range(2):
+                t0 = time.perf_counter()
+                oracle.iterate(e8, 2, 0, N_ADAPT, W.GAUSS, W.gauss_params(DIM, A), False,
+                               nthreads=t)
+                best = max(best, N_ADAPT / (time.perf_counter() - t0))
+            sweep[str(t)] = best
             t = t * 2 if t * 2 <= cores or t == cores else cores
         out["thread_scaling"] = {"unit": "samples/s", "samples_per_s_by_threads": sweep,
                                  "sample": "d=8 Gaussian, one fixed-grid iteration of 1e7 "
-                                           "samples on the uniform grid per thread count"}
+                                           "samples on the uniform grid per thread count, "
+                                           "the better of two runs"}
     return out
 
 
