@@ -845,7 +845,7 @@ def main():
                 # kernel build: fraction of elapsed cycles the pipe was busy)
                 "binding_pipe": {"pipe": "fmaheavy: integer multiplies (34 Philox + 8 bin "
                                          "32x32->64 products per d=8 sample)",
-                                 "busy_ncu": 0.735}}
+                                 "busy_ncu": 0.800}}
     if rank == 0 and "pipes" in legs:
         roofline["pipes"] = pipe_fractions(V, fixed_ms, statistics.median(adapt32_ns) / 1e6
                                            if adapt32_ns else None)
